@@ -1,0 +1,253 @@
+/*
+ * glm.h -- C ABI of libglm: s-step (communication-avoiding) mini-batch SGD
+ * for binary logistic regression and least squares / ridge on one GB300
+ * (sm_103a), after "Mixed-Precision Communication-Avoiding SGD for
+ * Generalized Linear Models on GPUs".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an int status (GLM_OK on success).  On failure,
+ *    glm_last_error() returns a thread-local, NUL-terminated description.
+ *  - Pointers are DEVICE pointers unless the argument says "host".  The
+ *    caller owns every buffer it passes; the library owns what a handle
+ *    allocates and frees it in glm_destroy / glm_batch_destroy.
+ *  - Matrices are row-major, with contiguous rows (stride = number of
+ *    columns) unless a leading dimension is given.
+ *  - Work is enqueued on the handle's stream and returns without waiting,
+ *    except glm_create*, glm_loss, glm_sample_indices with a host output
+ *    and glm_sync, which block.  Device-side checks (non-finite iterates)
+ *    raise a flag that glm_sync reports as GLM_ENONFINITE.
+ *  - Argument errors return GLM_EINVAL before anything is enqueued.
+ *
+ * Notation (paper Sec. 3.1): A in R^{m x n}, labels y, mini-batch b, s-step
+ * length s, step size eta, ridge weight lambda, alpha = eta / b,
+ * c = 1 - eta * lambda.  The objective is
+ *     F(x) = m^-1 sum_i L(a_i^T x, y_i) + (lambda/2) ||x||^2
+ * with L the logistic loss log(1 + exp(-y r)) or the squared loss
+ * (r - y)^2 / 2 (paper Sec. 2.1; the ridge term is this library's addition).
+ */
+#ifndef GLM_H_
+#define GLM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define GLM_OK 0
+#define GLM_EINVAL 1        /* invalid argument                                */
+#define GLM_ENOMEM 2        /* device allocation failed                        */
+#define GLM_ECUDA 3         /* a CUDA runtime / driver call failed             */
+#define GLM_ENONFINITE 4    /* a NaN or Inf was produced on the device         */
+#define GLM_ETIMEOUT 5      /* a bounded device wait gave up                   */
+#define GLM_EUNSUPPORTED 6  /* valid request this build does not support       */
+
+/* ---- losses (paper Sec. 2.1) -------------------------------------------- */
+#define GLM_LOGISTIC 0      /* labels must be -1 or +1 */
+#define GLM_LSQ 1           /* least squares / ridge   */
+
+/* ---- element types (paper Table 1 storage slots u_A, u_G, u_r, u_g) ------ */
+#define GLM_F32 0
+#define GLM_BF16 1
+#define GLM_F16 2
+#define GLM_TF32 3          /* FP32 container rounded to 10 mantissa bits      */
+#define GLM_E4M3 4          /* FP8 E4M3 with one power-of-two scale per row    */
+#define GLM_F64 5
+
+typedef struct glm_handle_s *glm_handle;
+
+/* Last error message of the calling thread ("" if none). */
+const char *glm_last_error(void);
+
+/* Library version string. */
+const char *glm_version(void);
+
+/* ---- dataset handles ----------------------------------------------------- */
+
+typedef struct {
+  int input_dtype;   /* element type behind the A pointer: GLM_F32 (float)
+                        or GLM_BF16 (uint16 bit patterns).  Default GLM_F32. */
+  int input_on_host; /* 1: A and y are host pointers; 0 (default): device.    */
+  int column_scales; /* 1 (default): BF16/F16 storage keeps one power-of-two
+                        scale per column (the value nearest the column RMS)
+                        and stores A/scale.                                    */
+  int fp8_copy;      /* 1: also keep an FP8-E4M3 copy of A with one
+                        power-of-two scale per row (needed by GLM_E4M3 Gram). */
+  void *stream;      /* cudaStream_t the handle enqueues on; NULL creates a
+                        private non-blocking stream owned by the handle (pass
+                        cudaStreamLegacy, 0x1, for the legacy default stream). */
+} glm_create_opts;
+
+/* Fill *o with the defaults documented above. */
+void glm_create_opts_default(glm_create_opts *o);
+
+/*
+ * Copy the dataset (A: m x n row-major, y: m labels) into handle-owned
+ * device storage of element type `dtype` (GLM_F32, GLM_BF16 or GLM_F16),
+ * paper Table 1 slot u_A; labels stay FP32.  The caller keeps ownership of
+ * A and y.  Requires 1 <= m < 2^31, 1 <= n <= 65536, loss GLM_LOGISTIC
+ * (labels exactly +-1, else GLM_EINVAL) or GLM_LSQ.  Blocks until the copy
+ * and conversion are done.  glm_create takes device FP32 pointers.
+ */
+int glm_create(const float *A, const float *y, int64_t m, int64_t n, int loss,
+               int dtype, glm_handle *out);
+int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n,
+                  int loss, int dtype, const glm_create_opts *opts,
+                  glm_handle *out);
+
+/* Release everything the handle owns.  NULL is accepted. */
+int glm_destroy(glm_handle h);
+
+/* Shape / stream queries. */
+int glm_shape(glm_handle h, int64_t *m, int64_t *n);
+void *glm_stream(glm_handle h);
+
+/* Wait for the handle's stream; returns GLM_ENONFINITE if a run since the
+ * previous glm_sync produced a non-finite value (the flag is then cleared). */
+int glm_sync(glm_handle h);
+
+/* ---- runs ---------------------------------------------------------------- */
+
+typedef struct {
+  int gram_dtype;     /* u_G: GLM_F32, GLM_TF32, GLM_BF16, GLM_F16 or GLM_E4M3;
+                         -1 (default) = the storage type.  Accumulation is
+                         always FP32 (paper Eq. for BF16-in/FP32-acc).       */
+  int gemv_dtype;     /* u_r = u_g (margin and outer-gradient operands);
+                         -1 (default) = gram_dtype, or the storage type when
+                         gram_dtype is GLM_E4M3.                              */
+  int recurrence_f64; /* u_c = u_sigma: -1 (default) FP64 iff s >= 32,
+                         0 FP32, 1 FP64.                                      */
+  int kahan;          /* 1 (default): Kahan-compensated FP32 Y^T u sums.      */
+  int64_t first_iter; /* SGD-equivalent iteration the run starts at; draws
+                         continue the counter-based stream from there, so a
+                         run of k+l iterations equals a run of k followed by
+                         a run of l with first_iter = k.  Default 0.         */
+  uint32_t problem;   /* stream id (second Philox key word).  Default 0.     */
+  int use_graph;      /* 1 (default): capture the run as a CUDA graph once
+                         per shape and replay it.                            */
+  int cluster;        /* CTAs cooperating on the x-dependent chain:
+                         0 (default) = automatic, else 1..16.                */
+  int64_t chunk_outer;/* outer iterations staged per chunk; 0 = automatic.   */
+  int gram_impl;      /* 0 (default) automatic, 1 SIMT FP32 kernel,
+                         2 tcgen05 tensor-core kernel.                        */
+} glm_ca_opts;
+
+void glm_ca_opts_default(glm_ca_opts *o);
+
+/*
+ * Plain mini-batch SGD (paper Sec. 2.1 / Sec. 3.1) in FP32 with FP32 master
+ * weights: per iteration t, draw b rows, z = Y x, u = dL/dr(z, y_I),
+ * x <- c x - alpha Y^T u.  x: device FP32[n], read as x_0 and overwritten
+ * with x_T.  iters >= 0, b >= 1, 0 <= eta*lambda < 1.
+ */
+int glm_sgd_run(glm_handle h, int64_t b, float eta, float lambda,
+                int64_t iters, uint64_t seed, float *x);
+int glm_sgd_run_ex(glm_handle h, int64_t b, float eta, float lambda,
+                   int64_t iters, uint64_t seed, float *x,
+                   const glm_ca_opts *opts);
+
+/*
+ * CA-SGD (paper Algorithm 1, with the ridge decay c).  Each outer iteration
+ * draws s*b indices, gathers Y (s b x n), forms r = Y x and the strictly
+ * block-lower Gram blocks G_{j,i} = Y_j Y_i^T (i < j), runs
+ *     z_j = c^j r_j - alpha sum_{i<j} c^{j-1-i} G_{j,i} u_i,
+ *     u_j = dL/dr(z_j, y_{I_j}),                       j = 0..s-1,
+ * and applies x <- c^s x - alpha sum_j c^{s-1-j} Y_j^T u_j.  In exact
+ * arithmetic this equals s SGD iterations on the same draws (paper
+ * Assumption 6).  If iters % s != 0 the last outer iteration has
+ * iters % s inner steps.  x: device FP32[n], in/out.
+ */
+int glm_ca_sgd_run(glm_handle h, int s, int64_t b, float eta, float lambda,
+                   int64_t iters, uint64_t seed, float *x);
+int glm_ca_sgd_run_ex(glm_handle h, int s, int64_t b, float eta, float lambda,
+                      int64_t iters, uint64_t seed, float *x,
+                      const glm_ca_opts *opts);
+
+/*
+ * F(x) = m^-1 sum_i L(a_i^T x, y_i) + (lambda/2) ||x||^2 over the stored
+ * data (paper Sec. 2.1), FP32 margins, Kahan-compensated FP32 per-thread
+ * sums, FP64 block totals.  x: device FP32[n]; *out: host double.  Blocks.
+ */
+int glm_loss(glm_handle h, const float *x, float lambda, double *out);
+
+/*
+ * Index stream (paper Algorithm 1, sampling step): out[i] = row of global
+ * draw first_draw + i, i.i.d. uniform on [0, m) with replacement.  Draw q
+ * takes 64-bit word q mod 4 of Philox4x64-10 block (q div 4, 0, 0, 0) under
+ * key (seed, problem) and maps it to floor(U m / 2^64).  out may be host or
+ * device memory (detected); count >= 0, 1 <= m < 2^31.  Blocks.
+ */
+int glm_sample_indices(uint64_t seed, uint32_t problem, int64_t first_draw,
+                       int64_t count, int64_t m, int32_t *out);
+
+/* ---- kernel-level entry points (tests, micro-benchmarks) ----------------- */
+
+/*
+ * Strictly block-lower Gram (paper Algorithm 1, Gram step; Sec. 5.2 G_L) of
+ * `nouter` consecutive row groups of Y.  Y: device, `nouter * s * b` rows of
+ * `ld` elements of type `dtype` (GLM_F32, GLM_TF32 (FP32 container),
+ * GLM_BF16, GLM_F16, GLM_E4M3 bytes); only the first n columns are read and
+ * columns n..ld-1 must be zero.  row_scale: device FP32 per row (E4M3 only,
+ * else NULL).  G: device FP32, for each group g the s(s-1)/2 blocks stored
+ * row-block by row-block: row l of block row j (1 <= j < s) holds the j*b
+ * values G[j b + l][0 .. j b) at offset g*b*b*s(s-1)/2 + b*b*j(j-1)/2 + l*j*b.
+ * impl: 0 auto, 1 SIMT FP32, 2 tcgen05.  ld must be a multiple of 64 for
+ * impl 2.  stream: cudaStream_t or NULL (legacy default stream).
+ */
+int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b,
+                   int64_t n, int64_t ld, const float *row_scale, float *G,
+                   int impl, void *stream);
+
+/* ---- batched fits -------------------------------------------------------- */
+
+typedef struct {
+  const void *A;     /* m x n, element type input_dtype, host or device    */
+  const float *y;    /* m labels                                           */
+  int64_t m, n;
+  int loss;          /* GLM_LOGISTIC or GLM_LSQ                            */
+  float lambda, eta;
+  int64_t iters;     /* SGD-equivalent iterations                          */
+  uint64_t seed;
+  int s;             /* 0: chosen by the autotuner                         */
+  int64_t b;         /* mini-batch size (required)                         */
+  int gram_dtype;    /* -1: chosen by the autotuner                        */
+} glm_problem_desc;
+
+typedef struct glm_batch_s *glm_batch;
+
+typedef struct {
+  int dtype;          /* storage type for every problem (default GLM_BF16) */
+  int input_dtype;    /* GLM_F32 (default) or GLM_BF16                      */
+  int input_on_host;  /* 1 (default): descriptors point to host memory      */
+  void *stream;       /* as glm_create_opts.stream                          */
+} glm_batch_opts;
+
+void glm_batch_opts_default(glm_batch_opts *o);
+
+/* Upload P independent problems.  Blocks. */
+int glm_batch_create(int P, const glm_problem_desc *descs,
+                     const glm_batch_opts *opts, glm_batch *out);
+
+/*
+ * Run every problem's CA-SGD fit in one persistent launch: CTAs take
+ * problems from a device work queue (longest first).  xs: host array of P
+ * device FP32[n_p] pointers, in/out.  status: host int[P] or NULL, filled
+ * with per-problem GLM_OK / GLM_ENONFINITE after completion.  Blocks.
+ */
+int glm_batch_run(glm_batch bt, float *const *xs, int *status);
+
+/* Per-problem risk F_p(x_p) into host double[P].  Blocks. */
+int glm_batch_loss(glm_batch bt, float *const *xs, double *out);
+
+/* The (s, b, gram dtype, cluster) the autotuner chose for problem p. */
+int glm_batch_choice(glm_batch bt, int p, int *s, int64_t *b, int *gram_dtype);
+
+int glm_batch_destroy(glm_batch bt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLM_H_ */

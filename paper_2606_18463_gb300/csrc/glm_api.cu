@@ -1,0 +1,624 @@
+// glm_api.cu -- the C ABI of libglm (declared in include/glm.h): dataset
+// handles, run orchestration (chunked staging of x-independent work, the
+// cluster chain, CUDA-graph capture and replay), risk evaluation and the
+// kernel-level entry points.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "glm_internal.cuh"
+
+namespace glm {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                 cudaGetErrorString(e) + ")";
+  return e == cudaErrorMemoryAllocation ? GLM_ENOMEM : GLM_ECUDA;
+}
+
+int DevBuf::ensure(size_t need) {
+  if (need <= bytes && ptr) return GLM_OK;
+  release();
+  cudaError_t e = cudaMalloc(&ptr, need ? need : 16);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    bytes = 0;
+    return cuda_error(e, "cudaMalloc(run scratch)");
+  }
+  bytes = need;
+  return GLM_OK;
+}
+
+void DevBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+bool RunKey::operator==(const RunKey &o) const {
+  return s == o.s && gram_dt == o.gram_dt && gemv_dt == o.gemv_dt && rec64 == o.rec64 &&
+         kahan == o.kahan && cluster == o.cluster && gram_impl == o.gram_impl &&
+         sgd == o.sgd && b == o.b && iters == o.iters && first_iter == o.first_iter &&
+         chunk == o.chunk && seed == o.seed && problem == o.problem && eta == o.eta &&
+         lambda == o.lambda && x == o.x;
+}
+
+int loss_partials_needed();
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void free_handle(Handle *h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->ygram.release();
+  h->ygemv.release();
+  h->ylab.release();
+  h->yscale.release();
+  h->gbuf.release();
+  cudaFree(h->A);
+  cudaFree(h->y);
+  cudaFree(h->colscale);
+  cudaFree(h->A8);
+  cudaFree(h->rowscale8);
+  cudaFree(h->dflag);
+  cudaFree(h->loss_partials);
+  cudaFree(h->loss_out);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+// Resolved options of one run.
+struct RunPlan {
+  int s = 1;
+  int64_t b = 1, iters = 0, H = 0, chunk = 1;
+  int gram_dt = GLM_F32, gemv_dt = GLM_F32, rec64 = 0, kahan = 1, cluster = 1;
+  int gram_impl = 1, sgd = 0, use_graph = 1;
+  int64_t ld_gram = 0, ld_gemv = 0;  // 0 ld_gemv: GEMV reads the Gram copy
+  float eta = 0.f, lambda = 0.f, alpha = 0.f;
+  double c = 1.0;
+  uint64_t seed = 0;
+  uint32_t problem = 0;
+  int64_t first_iter = 0;
+  float *x = nullptr;
+};
+
+int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
+            uint64_t seed, float *x, const glm_ca_opts *o, bool sgd, RunPlan &p) {
+  if (!h) return set_error(GLM_EINVAL, "null handle");
+  if (!x) return set_error(GLM_EINVAL, "x is NULL");
+  if (s < 1 || s > 256) return set_error(GLM_EINVAL, "s must be in [1, 256]");
+  if (b < 1 || b > 65536) return set_error(GLM_EINVAL, "b must be in [1, 65536]");
+  if (iters < 0) return set_error(GLM_EINVAL, "iters must be >= 0");
+  if (!(eta > 0.f) || !isfinite(eta)) return set_error(GLM_EINVAL, "eta must be finite and > 0");
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return set_error(GLM_EINVAL, "lambda must be >= 0");
+  const double c = 1.0 - (double)eta * (double)lambda;
+  if (!(c > 0.0)) return set_error(GLM_EINVAL, "eta * lambda must be < 1");
+  if ((double)(s - 1) * -log2(c) > 60.0)
+    return set_error(GLM_EUNSUPPORTED, "c^-(s-1) exceeds 2^60 (eta*lambda too large for s)");
+  glm_ca_opts d;
+  glm_ca_opts_default(&d);
+  if (!o) o = &d;
+  p.s = s;
+  p.b = b;
+  p.iters = iters;
+  p.eta = eta;
+  p.lambda = lambda;
+  p.alpha = (float)((double)eta / (double)b);
+  p.c = c;
+  p.seed = seed;
+  p.problem = o->problem;
+  p.first_iter = o->first_iter;
+  if (o->first_iter < 0) return set_error(GLM_EINVAL, "first_iter must be >= 0");
+  p.x = x;
+  p.sgd = sgd ? 1 : 0;
+  p.kahan = o->kahan ? 1 : 0;
+  p.use_graph = o->use_graph ? 1 : 0;
+  // precision slots
+  int gdt = o->gram_dtype < 0 ? h->dtype : o->gram_dtype;
+  if (sgd) gdt = (o->gram_dtype < 0) ? GLM_F32 : o->gram_dtype;
+  if (gdt != GLM_F32 && gdt != GLM_TF32 && gdt != GLM_BF16 && gdt != GLM_F16 && gdt != GLM_E4M3)
+    return set_error(GLM_EINVAL, "gram_dtype must be F32, TF32, BF16, F16 or E4M3");
+  if (gdt == GLM_E4M3 && !h->A8)
+    return set_error(GLM_EINVAL, "E4M3 Gram needs a handle created with fp8_copy = 1");
+  int vdt = o->gemv_dtype;
+  if (vdt < 0) vdt = (gdt == GLM_E4M3) ? h->dtype : gdt;
+  if (vdt != GLM_F32 && vdt != GLM_TF32 && vdt != GLM_BF16 && vdt != GLM_F16)
+    return set_error(GLM_EINVAL, "gemv_dtype must be F32, TF32, BF16 or F16");
+  p.gram_dt = gdt;
+  p.gemv_dt = vdt;
+  p.rec64 = o->recurrence_f64 < 0 ? (s >= 32 ? 1 : 0) : (o->recurrence_f64 ? 1 : 0);
+  p.ld_gram = round_up(h->n, 64);
+  p.ld_gemv = (vdt == gdt) ? 0 : round_up(h->n, 64);
+  // Gram implementation
+  if (o->gram_impl == 2 && !gram_tc_supported(gdt, p.ld_gram))
+    return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram does not support this operand type");
+  p.gram_impl = o->gram_impl == 0 ? (gram_tc_supported(gdt, p.ld_gram) ? 2 : 1) : o->gram_impl;
+  if (p.gram_impl != 1 && p.gram_impl != 2) return set_error(GLM_EINVAL, "gram_impl");
+  // chunking
+  p.H = (iters + s - 1) / s;
+  const int64_t sb = (int64_t)s * b;
+  const int64_t gsz = b * b * (int64_t)s * (s - 1) / 2;
+  const int64_t per_outer = sb * (p.ld_gram * elem_bytes(gdt) +
+                                  (p.ld_gemv ? p.ld_gemv * elem_bytes(vdt) : 0) + 8) +
+                            gsz * 4;
+  int64_t chunk = o->chunk_outer;
+  if (chunk <= 0) {
+    const int64_t budget = 64ll << 20;
+    chunk = std::max<int64_t>(1, budget / std::max<int64_t>(per_outer, 1));
+  }
+  chunk = std::min<int64_t>(chunk, std::max<int64_t>(p.H, 1));
+  chunk = std::min<int64_t>(chunk, 65535);
+  p.chunk = chunk;
+  // cluster
+  ChainArgs probe = {};
+  probe.dt = vdt;
+  probe.n = h->n;
+  probe.b = b;
+  probe.s = s;
+  probe.rec64 = p.rec64;
+  const int cmax = chain_max_cluster(probe);
+  if (cmax < 1)
+    return set_error(GLM_EUNSUPPORTED, "s*b too large for the on-chip recurrence state");
+  int C = o->cluster;
+  if (C <= 0) {
+    C = 1;
+    while (C < 16 && (int64_t)C * 64 < h->n) C *= 2;
+  }
+  if (C > cmax) C = cmax;
+  if (C < 1 || C > 16) return set_error(GLM_EINVAL, "cluster must be in [1, 16]");
+  p.cluster = C;
+  return GLM_OK;
+}
+
+int ensure_scratch(Handle *h, const RunPlan &p, bool &realloc) {
+  const int64_t sb = (int64_t)p.s * p.b;
+  const int64_t rows = p.chunk * sb;
+  const int64_t gsz = p.b * p.b * (int64_t)p.s * (p.s - 1) / 2;
+  void *before[5] = {h->ygram.ptr, h->ygemv.ptr, h->ylab.ptr, h->yscale.ptr, h->gbuf.ptr};
+  GLM_TRY(h->ygram.ensure((size_t)rows * p.ld_gram * elem_bytes(p.gram_dt)));
+  if (p.ld_gemv) GLM_TRY(h->ygemv.ensure((size_t)rows * p.ld_gemv * elem_bytes(p.gemv_dt)));
+  GLM_TRY(h->ylab.ensure((size_t)rows * 4));
+  GLM_TRY(h->yscale.ensure((size_t)rows * 4));
+  GLM_TRY(h->gbuf.ensure((size_t)std::max<int64_t>(1, p.chunk * gsz) * 4));
+  void *after[5] = {h->ygram.ptr, h->ygemv.ptr, h->ylab.ptr, h->yscale.ptr, h->gbuf.ptr};
+  realloc = memcmp(before, after, sizeof(before)) != 0;
+  return GLM_OK;
+}
+
+// Enqueue a whole run on stream st.
+int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
+  const int64_t sb = (int64_t)p.s * p.b;
+  ChainArgs ca;
+  memset(&ca, 0, sizeof(ca));
+  ca.dt = p.gemv_dt;
+  ca.Y = p.ld_gemv ? h->ygemv.ptr : h->ygram.ptr;
+  ca.ldy = p.ld_gemv ? p.ld_gemv : p.ld_gram;
+  ca.ylab = static_cast<const float *>(h->ylab.ptr);
+  ca.G = static_cast<const float *>(h->gbuf.ptr);
+  ca.x = p.x;
+  ca.flag = h->dflag;
+  ca.n = h->n;
+  ca.b = p.b;
+  ca.s = p.s;
+  ca.loss = h->loss;
+  ca.alpha = p.alpha;
+  ca.rec64 = p.rec64;
+  ca.kahan = p.kahan;
+  ca.cluster = p.cluster;
+  double cp = 1.0;
+  for (int j = 0; j <= p.s; ++j) {
+    ca.cpow[j] = cp;
+    ca.cinv[j] = 1.0 / cp;
+    cp *= p.c;
+  }
+  for (int64_t h0 = 0; h0 < p.H; h0 += p.chunk) {
+    const int64_t nout = std::min<int64_t>(p.chunk, p.H - h0);
+    const int64_t it0 = h0 * p.s;                          // first iteration of chunk
+    const int64_t it1 = std::min<int64_t>(p.iters, (h0 + nout) * p.s);
+    const int64_t rows = (it1 - it0) * p.b;
+    const int s_last = (int)(it1 - (h0 + nout - 1) * p.s);
+    GatherArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.A = h->A;
+    ga.lda = h->lda;
+    ga.a_dt = h->dtype;
+    ga.colscale = h->colscale;
+    ga.A8 = h->A8;
+    ga.rs8 = h->rowscale8;
+    ga.lda8 = h->lda8;
+    ga.y = h->y;
+    ga.m = h->m;
+    ga.n = h->n;
+    ga.rows = rows;
+    ga.q0 = (uint64_t)((p.first_iter + it0) * p.b);
+    ga.seed = p.seed;
+    ga.problem = p.problem;
+    ga.out1 = h->ygram.ptr;
+    ga.dt1 = p.gram_dt;
+    ga.ld1 = p.ld_gram;
+    if (p.ld_gemv) {
+      ga.out2 = h->ygemv.ptr;
+      ga.dt2 = p.gemv_dt;
+      ga.ld2 = p.ld_gemv;
+    }
+    ga.ylab = static_cast<float *>(h->ylab.ptr);
+    ga.rscale = static_cast<float *>(h->yscale.ptr);
+    GLM_TRY(launch_gather(ga, st));
+    if (p.s > 1) {
+      GramArgs gr;
+      gr.Y = h->ygram.ptr;
+      gr.dt = p.gram_dt;
+      gr.ld = p.ld_gram;
+      gr.rs = p.gram_dt == GLM_E4M3 ? static_cast<const float *>(h->yscale.ptr) : nullptr;
+      gr.nouter = nout;
+      gr.rows = rows;
+      gr.s = p.s;
+      gr.b = p.b;
+      gr.n = h->n;
+      gr.G = static_cast<float *>(h->gbuf.ptr);
+      if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, st));
+      else GLM_TRY(launch_gram_simt(gr, st));
+    }
+    ca.nouter = (int)nout;
+    ca.s_last = s_last;
+    GLM_TRY(launch_chain(ca, st));
+    (void)sb;
+  }
+  return GLM_OK;
+}
+
+int run_common(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
+               uint64_t seed, float *x, const glm_ca_opts *o, bool sgd) {
+  RunPlan p;
+  GLM_TRY(resolve(h, s, b, eta, lambda, iters, seed, x, o, sgd, p));
+  if (iters == 0) return GLM_OK;
+  bool realloc = false;
+  GLM_TRY(ensure_scratch(h, p, realloc));
+  if (!p.use_graph) return enqueue_run(h, p, h->stream);
+  RunKey key;
+  key.s = p.s; key.gram_dt = p.gram_dt; key.gemv_dt = p.gemv_dt; key.rec64 = p.rec64;
+  key.kahan = p.kahan; key.cluster = p.cluster; key.gram_impl = p.gram_impl; key.sgd = p.sgd;
+  key.b = p.b; key.iters = p.iters; key.first_iter = p.first_iter; key.chunk = p.chunk;
+  key.seed = p.seed; key.problem = p.problem; key.eta = p.eta; key.lambda = p.lambda;
+  key.x = p.x;
+  if (realloc && h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (!h->graph || !(h->graph_key == key)) {
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    cudaStream_t cap;
+    GLM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_error(e, "cudaStreamBeginCapture");
+    }
+    const int rc = enqueue_run(h, p, cap);
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (rc != GLM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->graph = nullptr;
+      return cuda_error(e, "cudaGraphInstantiate");
+    }
+    h->graph_key = key;
+  }
+  GLM_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
+  return GLM_OK;
+}
+
+}  // namespace
+}  // namespace glm
+
+using namespace glm;
+
+extern "C" {
+
+const char *glm_last_error(void) { return g_last_error.c_str(); }
+
+const char *glm_version(void) { return "libglm 0.1 (sm_103a)"; }
+
+void glm_create_opts_default(glm_create_opts *o) {
+  if (!o) return;
+  o->input_dtype = GLM_F32;
+  o->input_on_host = 0;
+  o->column_scales = 1;
+  o->fp8_copy = 0;
+  o->stream = nullptr;
+}
+
+void glm_ca_opts_default(glm_ca_opts *o) {
+  if (!o) return;
+  o->gram_dtype = -1;
+  o->gemv_dtype = -1;
+  o->recurrence_f64 = -1;
+  o->kahan = 1;
+  o->first_iter = 0;
+  o->problem = 0;
+  o->use_graph = 1;
+  o->cluster = 0;
+  o->chunk_outer = 0;
+  o->gram_impl = 0;
+}
+
+int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss, int dtype,
+                  const glm_create_opts *opts, glm_handle *out) {
+  g_last_error.clear();
+  if (!out) return set_error(GLM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A || !y) return set_error(GLM_EINVAL, "A or y is NULL");
+  if (m < 1 || m >= (1ll << 31)) return set_error(GLM_EINVAL, "m must be in [1, 2^31)");
+  if (n < 1 || n > 65536) return set_error(GLM_EINVAL, "n must be in [1, 65536]");
+  if (loss != GLM_LOGISTIC && loss != GLM_LSQ) return set_error(GLM_EINVAL, "unknown loss");
+  if (dtype != GLM_F32 && dtype != GLM_BF16 && dtype != GLM_F16)
+    return set_error(GLM_EINVAL, "storage dtype must be GLM_F32, GLM_BF16 or GLM_F16");
+  glm_create_opts d;
+  glm_create_opts_default(&d);
+  if (!opts) opts = &d;
+  if (opts->input_dtype != GLM_F32 && opts->input_dtype != GLM_BF16)
+    return set_error(GLM_EINVAL, "input_dtype must be GLM_F32 or GLM_BF16");
+  Handle *h = new Handle();
+  h->m = m;
+  h->n = n;
+  h->loss = loss;
+  h->dtype = dtype;
+  h->lda = round_up(n, 8);
+  int rc = GLM_OK;
+  auto fail = [&](int code) {
+    free_handle(h);
+    return code;
+  };
+#define CK(expr)                                                               \
+  do {                                                                         \
+    cudaError_t e_ = (expr);                                                   \
+    if (e_ != cudaSuccess) return fail(cuda_error(e_, #expr));                 \
+  } while (0)
+  if (opts->stream) {
+    h->stream = static_cast<cudaStream_t>(opts->stream);
+  } else {
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  cudaStream_t st = h->stream;
+  const int ieb = opts->input_dtype == GLM_BF16 ? 2 : 4;
+  const int eb = elem_bytes(dtype);
+  CK(cudaMalloc(&h->A, (size_t)m * h->lda * eb));
+  CK(cudaMalloc(&h->y, (size_t)m * 4));
+  CK(cudaMalloc(&h->dflag, 16));
+  CK(cudaMemsetAsync(h->dflag, 0, 16, st));
+  CK(cudaMalloc(&h->loss_partials, (size_t)loss_partials_needed() * 8));
+  CK(cudaMalloc(&h->loss_out, 8));
+  // input in device memory (temporary upload when it lives on the host)
+  const void *src = A;
+  const float *ysrc = y;
+  void *tmpA = nullptr;
+  float *tmpy = nullptr;
+  const bool host_in = opts->input_on_host || !is_device_ptr(A);
+  if (host_in) {
+    CK(cudaMalloc(&tmpA, (size_t)m * n * ieb));
+    CK(cudaMemcpyAsync(tmpA, A, (size_t)m * n * ieb, cudaMemcpyHostToDevice, st));
+    src = tmpA;
+  }
+  if (opts->input_on_host || !is_device_ptr(y)) {
+    CK(cudaMalloc(&tmpy, (size_t)m * 4));
+    CK(cudaMemcpyAsync(tmpy, y, (size_t)m * 4, cudaMemcpyHostToDevice, st));
+    ysrc = tmpy;
+  }
+  auto cleanup_tmp = [&]() {
+    if (tmpA) cudaFree(tmpA);
+    if (tmpy) cudaFree(tmpy);
+    tmpA = nullptr;
+    tmpy = nullptr;
+  };
+  CK(cudaMemcpyAsync(h->y, ysrc, (size_t)m * 4, cudaMemcpyDeviceToDevice, st));
+  // per-column power-of-two scales (BF16 / F16 storage)
+  if (dtype != GLM_F32 && opts->column_scales) {
+    double *acc = nullptr;
+    CK(cudaMalloc(&acc, (size_t)n * 8));
+    CK(cudaMemsetAsync(acc, 0, (size_t)n * 8, st));
+    rc = launch_colsumsq(src, opts->input_dtype, m, n, acc, st);
+    if (rc != GLM_OK) { cudaFree(acc); cleanup_tmp(); return fail(rc); }
+    std::vector<double> hs(n);
+    CK(cudaMemcpyAsync(hs.data(), acc, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cudaFree(acc);
+    std::vector<float> kappa(h->lda, 1.0f);
+    for (int64_t k = 0; k < n; ++k) {
+      const double rms = sqrt(hs[k] / (double)m);
+      kappa[k] = rms > 0.0 ? (float)ldexp(1.0, (int)nearbyint(log2(rms))) : 1.0f;
+    }
+    CK(cudaMalloc(&h->colscale, (size_t)h->lda * 4));
+    CK(cudaMemcpyAsync(h->colscale, kappa.data(), (size_t)h->lda * 4, cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaStreamSynchronize(st));
+  }
+  rc = launch_create_convert(h, src, opts->input_dtype, 0, m, st);
+  if (rc != GLM_OK) { cleanup_tmp(); return fail(rc); }
+  if (opts->fp8_copy) {
+    h->lda8 = round_up(n, 16);
+    CK(cudaMalloc(&h->A8, (size_t)m * h->lda8));
+    CK(cudaMalloc(&h->rowscale8, (size_t)m * 4));
+    rc = launch_fp8_copy(h, src, opts->input_dtype, 0, m, st);
+    if (rc != GLM_OK) { cleanup_tmp(); return fail(rc); }
+  }
+  rc = launch_check_labels(h->y, m, loss, h->dflag, st);
+  if (rc != GLM_OK) { cleanup_tmp(); return fail(rc); }
+  unsigned flag = 0;
+  CK(cudaMemcpyAsync(&flag, h->dflag, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cleanup_tmp();
+  if (flag & FLAG_BAD_LABEL)
+    return fail(set_error(GLM_EINVAL, loss == GLM_LOGISTIC
+                                          ? "logistic labels must be exactly -1 or +1"
+                                          : "labels must be finite"));
+#undef CK
+  *out = reinterpret_cast<glm_handle>(h);
+  return GLM_OK;
+}
+
+int glm_create(const float *A, const float *y, int64_t m, int64_t n, int loss, int dtype,
+               glm_handle *out) {
+  return glm_create_ex(A, y, m, n, loss, dtype, nullptr, out);
+}
+
+int glm_destroy(glm_handle hh) {
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h) return GLM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_handle(h);
+  return GLM_OK;
+}
+
+int glm_shape(glm_handle hh, int64_t *m, int64_t *n) {
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h) return set_error(GLM_EINVAL, "null handle");
+  if (m) *m = h->m;
+  if (n) *n = h->n;
+  return GLM_OK;
+}
+
+void *glm_stream(glm_handle hh) {
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  return h ? (void *)h->stream : nullptr;
+}
+
+int glm_sync(glm_handle hh) {
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h) return set_error(GLM_EINVAL, "null handle");
+  unsigned flag = 0;
+  GLM_CUDA_TRY(cudaMemcpyAsync(&flag, h->dflag, 4, cudaMemcpyDeviceToHost, h->stream));
+  GLM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (flag) {
+    GLM_CUDA_TRY(cudaMemsetAsync(h->dflag, 0, 4, h->stream));
+    GLM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (flag & FLAG_TIMEOUT) return set_error(GLM_ETIMEOUT, "a bounded device wait gave up");
+    return set_error(GLM_ENONFINITE, "a run produced a non-finite margin, residual or iterate");
+  }
+  return GLM_OK;
+}
+
+int glm_sgd_run_ex(glm_handle hh, int64_t b, float eta, float lambda, int64_t iters,
+                   uint64_t seed, float *x, const glm_ca_opts *opts) {
+  g_last_error.clear();
+  return run_common(reinterpret_cast<Handle *>(hh), 1, b, eta, lambda, iters, seed, x, opts,
+                    true);
+}
+
+int glm_sgd_run(glm_handle h, int64_t b, float eta, float lambda, int64_t iters, uint64_t seed,
+                float *x) {
+  return glm_sgd_run_ex(h, b, eta, lambda, iters, seed, x, nullptr);
+}
+
+int glm_ca_sgd_run_ex(glm_handle hh, int s, int64_t b, float eta, float lambda, int64_t iters,
+                      uint64_t seed, float *x, const glm_ca_opts *opts) {
+  g_last_error.clear();
+  return run_common(reinterpret_cast<Handle *>(hh), s, b, eta, lambda, iters, seed, x, opts,
+                    false);
+}
+
+int glm_ca_sgd_run(glm_handle h, int s, int64_t b, float eta, float lambda, int64_t iters,
+                   uint64_t seed, float *x) {
+  return glm_ca_sgd_run_ex(h, s, b, eta, lambda, iters, seed, x, nullptr);
+}
+
+int glm_loss(glm_handle hh, const float *x, float lambda, double *out) {
+  g_last_error.clear();
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h || !x || !out) return set_error(GLM_EINVAL, "null argument");
+  if (!(lambda >= 0.f)) return set_error(GLM_EINVAL, "lambda must be >= 0");
+  GLM_TRY(launch_loss(h, x, lambda, h->stream));
+  GLM_CUDA_TRY(cudaMemcpyAsync(out, h->loss_out, 8, cudaMemcpyDeviceToHost, h->stream));
+  GLM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return GLM_OK;
+}
+
+int glm_sample_indices(uint64_t seed, uint32_t problem, int64_t first_draw, int64_t count,
+                       int64_t m, int32_t *out) {
+  g_last_error.clear();
+  if (count < 0 || first_draw < 0) return set_error(GLM_EINVAL, "count/first_draw must be >= 0");
+  if (m < 1 || m >= (1ll << 31)) return set_error(GLM_EINVAL, "m must be in [1, 2^31)");
+  if (count == 0) return GLM_OK;
+  if (!out) return set_error(GLM_EINVAL, "out is NULL");
+  if (is_device_ptr(out)) {
+    GLM_TRY(launch_sample(seed, problem, first_draw, count, m, out, 0));
+    GLM_CUDA_TRY(cudaStreamSynchronize(0));
+    return GLM_OK;
+  }
+  int32_t *d = nullptr;
+  GLM_CUDA_TRY(cudaMalloc(&d, (size_t)count * 4));
+  int rc = launch_sample(seed, problem, first_draw, count, m, d, 0);
+  if (rc == GLM_OK) {
+    cudaError_t e = cudaMemcpy(out, d, (size_t)count * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpy(indices)");
+  }
+  cudaFree(d);
+  return rc;
+}
+
+int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b, int64_t n,
+                   int64_t ld, const float *row_scale, float *G, int impl, void *stream) {
+  g_last_error.clear();
+  if (!Y || !G) return set_error(GLM_EINVAL, "null argument");
+  if (nouter < 1 || s < 2 || b < 1 || n < 1 || ld < n || ld % 8)
+    return set_error(GLM_EINVAL, "bad Gram shape (need nouter>=1, s>=2, b>=1, n<=ld, ld%8==0)");
+  if (dtype != GLM_F32 && dtype != GLM_TF32 && dtype != GLM_BF16 && dtype != GLM_F16 &&
+      dtype != GLM_E4M3)
+    return set_error(GLM_EINVAL, "bad Gram operand type");
+  if (dtype == GLM_E4M3 && (!row_scale || ld % 16))
+    return set_error(GLM_EINVAL, "E4M3 Gram needs row scales and ld % 16 == 0");
+  GramArgs a;
+  a.Y = Y;
+  a.dt = dtype;
+  a.ld = ld;
+  a.rs = dtype == GLM_E4M3 ? row_scale : nullptr;
+  a.nouter = nouter;
+  a.rows = nouter * s * b;
+  a.s = s;
+  a.b = b;
+  a.n = n;
+  a.G = G;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (impl == 0) impl = gram_tc_supported(dtype, ld) ? 2 : 1;
+  if (impl == 2) {
+    if (!gram_tc_supported(dtype, ld))
+      return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram: unsupported type or ld % 64 != 0");
+    return launch_gram_tc(a, st);
+  }
+  if (impl != 1) return set_error(GLM_EINVAL, "impl must be 0, 1 or 2");
+  return launch_gram_simt(a, st);
+}
+
+// ---- batched fits: implemented in glm_batch.cu -----------------------------
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+// glm_internal.cuh -- shared device helpers and host-side structures of
+// libglm (CA-SGD for GLMs on sm_103a).  Nothing here is visible through the
+// C ABI; see include/glm.h for the public contract.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "glm.h"
+
+namespace glm {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local last error, see glm_last_error)
+// ---------------------------------------------------------------------------
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+
+#define GLM_CUDA_TRY(expr)                                                     \
+  do {                                                                         \
+    cudaError_t e_ = (expr);                                                   \
+    if (e_ != cudaSuccess) return ::glm::cuda_error(e_, #expr);                \
+  } while (0)
+
+#define GLM_TRY(expr)                                                          \
+  do {                                                                         \
+    int rc_ = (expr);                                                          \
+    if (rc_ != GLM_OK) return rc_;                                             \
+  } while (0)
+
+// Device flag bits (one uint32 per handle, raised with atomicOr).
+enum : unsigned {
+  FLAG_NONFINITE = 1u,
+  FLAG_BAD_LABEL = 2u,
+  FLAG_TIMEOUT = 4u,
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) on the device.
+// Counter (k, 0, 0, 0), key (seed, problem); draw q uses word q & 3 of block
+// q >> 2 and becomes row floor(U * m / 2^64).
+// ---------------------------------------------------------------------------
+struct U64x4 {
+  uint64_t v[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t k_lo, uint64_t k_hi,
+                                               uint64_t c0) {
+  const uint64_t kMul0 = 0xD2E7470EE14C6C93ull, kMul1 = 0xCA5A826395121157ull;
+  const uint64_t kWeyl0 = 0x9E3779B97F4A7C15ull, kWeyl1 = 0xBB67AE8584CAA73Bull;
+  uint64_t x0 = c0, x1 = 0, x2 = 0, x3 = 0;
+  uint64_t k0 = k_lo, k1 = k_hi;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(kMul0, x0), lo0 = kMul0 * x0;
+    const uint64_t hi1 = __umul64hi(kMul1, x2), lo1 = kMul1 * x2;
+    const uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+    x0 = n0;
+    x1 = lo1;
+    x2 = n2;
+    x3 = lo0;
+    k0 += kWeyl0;
+    k1 += kWeyl1;
+  }
+  U64x4 o;
+  o.v[0] = x0; o.v[1] = x1; o.v[2] = x2; o.v[3] = x3;
+  return o;
+}
+
+__device__ __forceinline__ int32_t draw_row(uint64_t seed, uint64_t problem,
+                                            uint64_t q, uint64_t m) {
+  const U64x4 blk = philox4x64_10(seed, problem, q >> 2);
+  const uint64_t w = blk.v[q & 3];
+  return (int32_t)__umul64hi(w, m);
+}
+
+// ---------------------------------------------------------------------------
+// Element conversions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_round(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// Load 8 consecutive storage elements as floats.
+template <typename T> struct Vec8;
+
+template <> struct Vec8<float> {
+  __device__ __forceinline__ static void load(const float *p, float (&o)[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+  }
+};
+
+template <> struct Vec8<__nv_bfloat16> {
+  __device__ __forceinline__ static void load(const __nv_bfloat16 *p,
+                                              float (&o)[8]) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[2 * i] = __uint_as_float(w[i] << 16);
+      o[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+  }
+};
+
+template <> struct Vec8<__half> {
+  __device__ __forceinline__ static void load(const __half *p, float (&o)[8]) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = *reinterpret_cast<const __half2 *>(&w[i]);
+      float2 f = __half22float2(h);
+      o[2 * i] = f.x;
+      o[2 * i + 1] = f.y;
+    }
+  }
+};
+
+// Store 8 floats as element type `dt` (GLM_F32 / GLM_TF32 / GLM_BF16 /
+// GLM_F16), rounding to nearest (ties to even; TF32 ties away).
+__device__ __forceinline__ void store8(void *dst, int dt, const float (&v)[8]) {
+  if (dt == GLM_F32 || dt == GLM_TF32) {
+    float w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = (dt == GLM_TF32) ? tf32_round(v[i]) : v[i];
+    float4 *d = reinterpret_cast<float4 *>(dst);
+    d[0] = make_float4(w[0], w[1], w[2], w[3]);
+    d[1] = make_float4(w[4], w[5], w[6], w[7]);
+  } else if (dt == GLM_BF16) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {  // GLM_F16
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+__host__ __device__ inline int elem_bytes(int dt) {
+  switch (dt) {
+  case GLM_F32: case GLM_TF32: return 4;
+  case GLM_BF16: case GLM_F16: return 2;
+  case GLM_E4M3: return 1;
+  case GLM_F64: return 8;
+  }
+  return 0;
+}
+
+__host__ __device__ inline int64_t round_up(int64_t v, int64_t a) {
+  return (v + a - 1) / a * a;
+}
+
+// ---------------------------------------------------------------------------
+// Losses (paper Sec. 2.1): u = dL/dr and L itself
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T dloss(int loss, T z, T y);
+
+template <> __device__ __forceinline__ float dloss<float>(int loss, float z, float y) {
+  if (loss == GLM_LOGISTIC) {
+    // -y * sigma(-y z) computed without overflow
+    const float t = y * z;
+    const float e = expf(-fabsf(t));
+    const float sig_neg_t = (t >= 0.f) ? e / (1.f + e) : 1.f / (1.f + e);
+    return -y * sig_neg_t;
+  }
+  return z - y;
+}
+
+template <> __device__ __forceinline__ double dloss<double>(int loss, double z, double y) {
+  if (loss == GLM_LOGISTIC) {
+    const double t = y * z;
+    const double e = exp(-fabs(t));
+    const double sig_neg_t = (t >= 0.0) ? e / (1.0 + e) : 1.0 / (1.0 + e);
+    return -y * sig_neg_t;
+  }
+  return z - y;
+}
+
+__device__ __forceinline__ float loss_term(int loss, float z, float y) {
+  if (loss == GLM_LOGISTIC) {
+    const float t = y * z;
+    return fmaxf(-t, 0.f) + log1pf(expf(-fabsf(t)));
+  }
+  const float d = z - y;
+  return 0.5f * d * d;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side structures
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need);
+  void release();
+  ~DevBuf() { release(); }
+};
+
+struct RunKey {
+  int s = 0, gram_dt = 0, gemv_dt = 0, rec64 = 0, kahan = 0, cluster = 0,
+      gram_impl = 0, sgd = 0;
+  int64_t b = 0, iters = 0, first_iter = 0, chunk = 0;
+  uint64_t seed = 0;
+  uint32_t problem = 0;
+  float eta = 0.f, lambda = 0.f;
+  float *x = nullptr;
+  bool operator==(const RunKey &o) const;
+};
+
+struct Handle {
+  int64_t m = 0, n = 0, lda = 0;
+  int loss = GLM_LOGISTIC, dtype = GLM_F32;
+  void *A = nullptr;            // m x lda storage elements
+  float *y = nullptr;           // m labels
+  float *colscale = nullptr;    // n power-of-two scales, or null
+  uint8_t *A8 = nullptr;        // optional FP8-E4M3 copy, m x lda8
+  float *rowscale8 = nullptr;   // its per-row scales
+  int64_t lda8 = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  unsigned *dflag = nullptr;    // device flag word
+  double *loss_partials = nullptr;
+  double *loss_out = nullptr;   // device double
+  // run scratch
+  DevBuf ygram, ygemv, ylab, yscale, gbuf;
+  // captured run graph
+  cudaGraphExec_t graph = nullptr;
+  RunKey graph_key;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (implemented in the k_*.cu files)
+// ---------------------------------------------------------------------------
+struct GatherArgs {
+  const void *A; int64_t lda; int a_dt;        // storage
+  const float *colscale;                       // or null
+  const uint8_t *A8; const float *rs8; int64_t lda8;  // FP8 copy (E4M3 out)
+  const float *y;
+  int64_t m, n, rows;                          // rows to gather
+  uint64_t q0, seed, problem;                  // first global draw
+  void *out1; int dt1; int64_t ld1;            // primary output (gram operand)
+  void *out2; int dt2; int64_t ld2;            // optional second output
+  float *ylab; float *rscale;                  // labels / row scales (E4M3)
+};
+int launch_gather(const GatherArgs &a, cudaStream_t st);
+
+struct GramArgs {
+  const void *Y; int dt; int64_t ld;
+  const float *rs;        // row scales (E4M3) or null
+  int64_t nouter, rows;   // rows valid in total (tail masking)
+  int s; int64_t b, n;
+  float *G;
+};
+int launch_gram_simt(const GramArgs &a, cudaStream_t st);
+int launch_gram_tc(const GramArgs &a, cudaStream_t st);
+bool gram_tc_supported(int dt, int64_t ld);
+
+struct ChainArgs {
+  const void *Y; int dt; int64_t ldy;
+  const float *ylab;
+  const float *G;
+  float *x;
+  unsigned *flag;
+  int64_t n, b;
+  int s, s_last, nouter, loss;
+  float alpha;
+  int rec64, kahan, cluster;
+  double cpow[257];    // c^j, j = 0..s
+  double cinv[257];    // c^-j
+};
+int launch_chain(const ChainArgs &a, cudaStream_t st);
+int chain_max_cluster(const ChainArgs &a);
+
+int launch_loss(Handle *h, const float *x, float lambda, cudaStream_t st);
+int launch_sample(uint64_t seed, uint64_t problem, int64_t first, int64_t count,
+                  int64_t m, int32_t *out, cudaStream_t st);
+int launch_create_convert(Handle *h, const void *src, int src_dt, int64_t row0,
+                          int64_t rows, cudaStream_t st);
+int launch_colsumsq(const void *src, int src_dt, int64_t rows, int64_t n,
+                    double *acc, cudaStream_t st);
+int launch_fp8_copy(Handle *h, const void *src, int src_dt, int64_t row0,
+                    int64_t rows, cudaStream_t st);
+int launch_check_labels(const float *y, int64_t m, int loss, unsigned *flag,
+                        cudaStream_t st);
+
+}  // namespace glm

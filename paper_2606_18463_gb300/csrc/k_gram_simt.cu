@@ -1,0 +1,132 @@
+// k_gram_simt.cu -- strictly block-lower Gram G_{j,i} = Y_j Y_i^T, i < j
+// (paper Algorithm 1, Gram step; only G_{j,<j} is ever read), with true FP32
+// FMA accumulation on the CUDA cores.  It is the FP32 (Recipe A) Gram, which
+// must not fall back to TF32, and the reference-shaped fallback for the other
+// operand types: BF16 / F16 / TF32 / E4M3 products are exact in FP32, so only
+// the accumulation order differs from the tensor-core kernel.
+//
+// Tiles of 64 x 64 outputs over the lower triangle of each outer step's
+// (s b) x (s b) Gram; 256 threads, 4 x 4 outputs per thread, K staged 32 at a
+// time through shared memory (stored k-major so a thread reads 4 rows with
+// one 16-byte load).
+#include "glm_internal.cuh"
+
+namespace glm {
+namespace {
+
+constexpr int kTile = 64, kK = 32, kThreads = 256;
+
+__device__ __forceinline__ void load8_any(const void *base, int dt, int64_t off,
+                                          float (&o)[8]) {
+  if (dt == GLM_F32 || dt == GLM_TF32) {
+    Vec8<float>::load(static_cast<const float *>(base) + off, o);
+  } else if (dt == GLM_BF16) {
+    Vec8<__nv_bfloat16>::load(static_cast<const __nv_bfloat16 *>(base) + off, o);
+  } else if (dt == GLM_F16) {
+    Vec8<__half>::load(static_cast<const __half *>(base) + off, o);
+  } else {  // E4M3 bytes
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(
+        static_cast<const uint8_t *>(base) + off));
+    const uint32_t ww[2] = {w.x, w.y};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const __nv_fp8_storage_t byte = (ww[i >> 2] >> (8 * (i & 3))) & 0xFF;
+      const __half_raw hr = __nv_cvt_fp8_to_halfraw(byte, __NV_E4M3);
+      o[i] = __half2float(__half(hr));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_gram_simt(GramArgs a) {
+  const int64_t sb = (int64_t)a.s * a.b;
+  const int64_t g = blockIdx.y;
+  const int64_t rows_g = min(sb, a.rows - g * sb);
+  // lower-triangular tile pair (TJ >= TI) from the linear block index
+  const int64_t t = blockIdx.x;
+  int64_t TJ = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (TJ * (TJ + 1) / 2 > t) --TJ;
+  while ((TJ + 1) * (TJ + 2) / 2 <= t) ++TJ;
+  const int64_t TI = t - TJ * (TJ + 1) / 2;
+  const int64_t r0 = TJ * kTile, c0 = TI * kTile;
+  const int64_t r_last = min(r0 + kTile, rows_g) - 1;
+  if (r_last < r0 || r_last / a.b <= c0 / a.b) return;  // nothing strictly lower
+
+  __shared__ __align__(16) float As[kK][kTile];
+  __shared__ __align__(16) float Bs[kK][kTile];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4] = {};
+  const int eb = elem_bytes(a.dt);
+  const char *Yg = static_cast<const char *>(a.Y) + g * sb * a.ld * eb;
+  // loader mapping: 256 threads x 8 k-values = 64 rows x 32 k
+  const int lrow = tid >> 2, lk = (tid & 3) * 8;
+  for (int64_t k0 = 0; k0 < a.n; k0 += kK) {
+    float va[8], vb[8];
+    const int64_t ra = r0 + lrow, rb = c0 + lrow;
+    if (ra < rows_g && k0 + lk < a.n) load8_any(Yg, a.dt, ra * a.ld + k0 + lk, va);
+    else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) va[i] = 0.f;
+    }
+    if (rb < rows_g && k0 + lk < a.n) load8_any(Yg, a.dt, rb * a.ld + k0 + lk, vb);
+    else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) vb[i] = 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      As[lk + i][lrow] = va[i];
+      Bs[lk + i][lrow] = vb[i];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kK; ++k) {
+      const float4 av = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+      const float ar[4] = {av.x, av.y, av.z, av.w};
+      const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+    }
+  }
+  // epilogue: strictly block-lower entries into the row-block layout
+  const int64_t bb = a.b * a.b;
+  float *Gg = a.G + g * (bb * a.s * (a.s - 1) / 2);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t rho = r0 + ty * 4 + i;
+    if (rho >= rows_g) continue;
+    const int64_t j = rho / a.b, l = rho - j * a.b;
+    float *grow = Gg + bb * (j * (j - 1) / 2) + l * (j * a.b);
+    const float sr = a.rs ? a.rs[g * sb + rho] : 1.f;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int64_t col = c0 + tx * 4 + jj;
+      if (col < j * a.b) {
+        float v = acc[i][jj];
+        if (a.rs) v = v * sr * a.rs[g * sb + col];
+        grow[col] = v;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int launch_gram_simt(const GramArgs &a, cudaStream_t st) {
+  if (a.s < 2 || a.nouter <= 0) return GLM_OK;
+  const int64_t sb = (int64_t)a.s * a.b;
+  const int64_t T = (sb + kTile - 1) / kTile;
+  const int64_t pairs = T * (T + 1) / 2;
+  if (pairs > 0x7fffffff || a.nouter > 65535)
+    return set_error(GLM_EINVAL, "gram: problem too large for one launch");
+  dim3 grid((unsigned)pairs, (unsigned)a.nouter);
+  k_gram_simt<<<grid, kThreads, 0, st>>>(a);
+  GLM_CUDA_TRY(cudaGetLastError());
+  return GLM_OK;
+}
+
+}  // namespace glm

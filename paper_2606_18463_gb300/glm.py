@@ -1,0 +1,284 @@
+"""ctypes binding of libglm (include/glm.h).
+
+Argument marshalling only: every step of SGD / CA-SGD runs in the CUDA
+kernels of libglm.so.  Functions keep the C names (``glm_create``,
+``glm_ca_sgd_run`` ...); ``Dataset`` is a thin convenience wrapper that owns a
+handle and accepts torch tensors (device memory and streams come from
+PyTorch) or numpy arrays (host memory).
+
+Importing this module does not load the library; the first call does, and
+raises ``ImportError`` if libglm.so has not been built -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libglm.so")
+
+# status codes
+GLM_OK, GLM_EINVAL, GLM_ENOMEM, GLM_ECUDA, GLM_ENONFINITE, GLM_ETIMEOUT, GLM_EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "GLM_OK", 1: "GLM_EINVAL", 2: "GLM_ENOMEM", 3: "GLM_ECUDA",
+                4: "GLM_ENONFINITE", 5: "GLM_ETIMEOUT", 6: "GLM_EUNSUPPORTED"}
+# losses
+GLM_LOGISTIC, GLM_LSQ = 0, 1
+# element types
+GLM_F32, GLM_BF16, GLM_F16, GLM_TF32, GLM_E4M3, GLM_F64 = range(6)
+DTYPES = {"f32": GLM_F32, "bf16": GLM_BF16, "f16": GLM_F16, "tf32": GLM_TF32,
+          "e4m3": GLM_E4M3, "f64": GLM_F64}
+
+# every symbol include/glm.h declares (checked by the CPU test-suite)
+EXPORTED = [
+    "glm_last_error", "glm_version", "glm_create_opts_default", "glm_create",
+    "glm_create_ex", "glm_destroy", "glm_shape", "glm_stream", "glm_sync",
+    "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_ca_sgd_run",
+    "glm_ca_sgd_run_ex", "glm_loss", "glm_sample_indices", "glm_gram_lower",
+    "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
+    "glm_batch_choice", "glm_batch_destroy",
+]
+
+
+class GlmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class glm_create_opts(ctypes.Structure):
+    _fields_ = [("input_dtype", ctypes.c_int), ("input_on_host", ctypes.c_int),
+                ("column_scales", ctypes.c_int), ("fp8_copy", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class glm_ca_opts(ctypes.Structure):
+    _fields_ = [("gram_dtype", ctypes.c_int), ("gemv_dtype", ctypes.c_int),
+                ("recurrence_f64", ctypes.c_int), ("kahan", ctypes.c_int),
+                ("first_iter", ctypes.c_int64), ("problem", ctypes.c_uint32),
+                ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
+                ("chunk_outer", ctypes.c_int64), ("gram_impl", ctypes.c_int)]
+
+
+class glm_problem_desc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("loss", ctypes.c_int),
+                ("lambda_", ctypes.c_float), ("eta", ctypes.c_float),
+                ("iters", ctypes.c_int64), ("seed", ctypes.c_uint64), ("s", ctypes.c_int),
+                ("b", ctypes.c_int64), ("gram_dtype", ctypes.c_int)]
+
+
+class glm_batch_opts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("input_dtype", ctypes.c_int),
+                ("input_on_host", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load libglm.so (ImportError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libglm.so not built ({LIB_PATH}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, u64, i32, f32 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_int, ctypes.c_float)
+        sig = {
+            "glm_last_error": ([], ctypes.c_char_p),
+            "glm_version": ([], ctypes.c_char_p),
+            "glm_create_opts_default": ([ctypes.POINTER(glm_create_opts)], None),
+            "glm_create": ([vp, vp, i64, i64, i32, i32, ctypes.POINTER(vp)], i32),
+            "glm_create_ex": ([vp, vp, i64, i64, i32, i32, ctypes.POINTER(glm_create_opts),
+                               ctypes.POINTER(vp)], i32),
+            "glm_destroy": ([vp], i32),
+            "glm_shape": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
+            "glm_stream": ([vp], vp),
+            "glm_sync": ([vp], i32),
+            "glm_ca_opts_default": ([ctypes.POINTER(glm_ca_opts)], None),
+            "glm_sgd_run": ([vp, i64, f32, f32, i64, u64, vp], i32),
+            "glm_sgd_run_ex": ([vp, i64, f32, f32, i64, u64, vp,
+                                ctypes.POINTER(glm_ca_opts)], i32),
+            "glm_ca_sgd_run": ([vp, i32, i64, f32, f32, i64, u64, vp], i32),
+            "glm_ca_sgd_run_ex": ([vp, i32, i64, f32, f32, i64, u64, vp,
+                                   ctypes.POINTER(glm_ca_opts)], i32),
+            "glm_loss": ([vp, vp, f32, ctypes.POINTER(ctypes.c_double)], i32),
+            "glm_sample_indices": ([u64, ctypes.c_uint32, i64, i64, i64, vp], i32),
+            "glm_gram_lower": ([vp, i32, i64, i32, i64, i64, i64, vp, vp, i32, vp], i32),
+            "glm_batch_opts_default": ([ctypes.POINTER(glm_batch_opts)], None),
+            "glm_batch_create": ([i32, ctypes.POINTER(glm_problem_desc),
+                                  ctypes.POINTER(glm_batch_opts), ctypes.POINTER(vp)], i32),
+            "glm_batch_run": ([vp, ctypes.POINTER(vp), ctypes.POINTER(i32)], i32),
+            "glm_batch_loss": ([vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)], i32),
+            "glm_batch_choice": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i32)], i32),
+            "glm_batch_destroy": ([vp], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def glm_last_error() -> str:
+    return load().glm_last_error().decode()
+
+
+def glm_version() -> str:
+    return load().glm_version().decode()
+
+
+def _check(rc: int):
+    if rc != GLM_OK:
+        raise GlmError(rc, glm_last_error())
+    return rc
+
+
+def _ptr(t) -> int:
+    """Data pointer of a torch tensor or numpy array (None -> 0)."""
+    if t is None:
+        return 0
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def default_create_opts() -> glm_create_opts:
+    o = glm_create_opts()
+    load().glm_create_opts_default(ctypes.byref(o))
+    return o
+
+
+def default_ca_opts(**kw) -> glm_ca_opts:
+    o = glm_ca_opts()
+    load().glm_ca_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k in ("gram_dtype", "gemv_dtype") and isinstance(v, str):
+            v = DTYPES[v]
+        setattr(o, k, v)
+    return o
+
+
+# ---- thin same-name wrappers -------------------------------------------------
+def glm_create_ex(A, y, m, n, loss, dtype, opts=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().glm_create_ex(_ptr(A), _ptr(y), m, n, loss, dtype,
+                                ctypes.byref(opts) if opts is not None else None,
+                                ctypes.byref(h)))
+    return h.value
+
+
+def glm_create(A, y, m, n, loss, dtype) -> int:
+    h = ctypes.c_void_p()
+    _check(load().glm_create(_ptr(A), _ptr(y), m, n, loss, dtype, ctypes.byref(h)))
+    return h.value
+
+
+def glm_destroy(h) -> None:
+    _check(load().glm_destroy(h))
+
+
+def glm_sync(h) -> int:
+    return load().glm_sync(h)
+
+
+def glm_sgd_run(h, b, eta, lam, iters, seed, x, opts=None) -> None:
+    if opts is None:
+        _check(load().glm_sgd_run(h, b, eta, lam, iters, seed, _ptr(x)))
+    else:
+        _check(load().glm_sgd_run_ex(h, b, eta, lam, iters, seed, _ptr(x), ctypes.byref(opts)))
+
+
+def glm_ca_sgd_run(h, s, b, eta, lam, iters, seed, x, opts=None) -> None:
+    if opts is None:
+        _check(load().glm_ca_sgd_run(h, s, b, eta, lam, iters, seed, _ptr(x)))
+    else:
+        _check(load().glm_ca_sgd_run_ex(h, s, b, eta, lam, iters, seed, _ptr(x),
+                                        ctypes.byref(opts)))
+
+
+def glm_loss(h, x, lam) -> float:
+    out = ctypes.c_double()
+    _check(load().glm_loss(h, _ptr(x), lam, ctypes.byref(out)))
+    return out.value
+
+
+def glm_sample_indices(seed, problem, first_draw, count, m, out) -> None:
+    _check(load().glm_sample_indices(seed, problem, first_draw, count, m, _ptr(out)))
+
+
+def glm_gram_lower(Y, dtype, nouter, s, b, n, ld, row_scale, G, impl=0, stream=None) -> None:
+    _check(load().glm_gram_lower(_ptr(Y), dtype, nouter, s, b, n, ld, _ptr(row_scale),
+                                 _ptr(G), impl, stream))
+
+
+def glm_stream(h) -> int:
+    return load().glm_stream(h)
+
+
+# ---- convenience wrapper -------------------------------------------------------
+class Dataset:
+    """Owns a libglm dataset handle.
+
+    A: (m, n) float32 (or BF16 bit patterns as int16/uint16 with
+    ``input_dtype='bf16'``), torch tensor (host or device) or numpy array;
+    y: (m,) float32.  ``dtype`` is the storage type ('f32', 'bf16', 'f16').
+    ``stream``: a torch.cuda.Stream (default: the current stream)."""
+
+    def __init__(self, A, y, loss, dtype="f32", *, fp8_copy=False, column_scales=True,
+                 input_dtype="f32", stream=None):
+        import torch
+        m, n = int(A.shape[0]), int(A.shape[1])
+        o = default_create_opts()
+        o.input_dtype = DTYPES[input_dtype]
+        on_host = not (hasattr(A, "is_cuda") and A.is_cuda)
+        o.input_on_host = 1 if on_host else 0
+        o.column_scales = 1 if column_scales else 0
+        o.fp8_copy = 1 if fp8_copy else 0
+        st = stream if stream is not None else torch.cuda.current_stream()
+        # the legacy default stream has handle 0, which the C ABI reads as
+        # "make a private stream"; pass cudaStreamLegacy (0x1) instead
+        o.stream = st.cuda_stream or 1
+        self.stream = st
+        if hasattr(A, "contiguous"):
+            A = A.contiguous()
+        if hasattr(y, "contiguous"):
+            y = y.contiguous()
+        self._keep = (A, y)
+        self.m, self.n, self.loss = m, n, loss
+        self.h = glm_create_ex(A, y, m, n, loss, DTYPES[dtype] if isinstance(dtype, str)
+                               else dtype, o)
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            glm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sgd(self, x, b, eta, lam, iters, seed, **opts):
+        glm_sgd_run(self.h, b, eta, lam, iters, seed, x,
+                    default_ca_opts(**opts) if opts else None)
+
+    def ca_sgd(self, x, s, b, eta, lam, iters, seed, **opts):
+        glm_ca_sgd_run(self.h, s, b, eta, lam, iters, seed, x,
+                       default_ca_opts(**opts) if opts else None)
+
+    def loss_value(self, x, lam) -> float:
+        return glm_loss(self.h, x, lam)
+
+    def sync(self):
+        _check(glm_sync(self.h))

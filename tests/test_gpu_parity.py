@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (written here, derived in the design notes):
+  * indices: bit-exact;
+  * FP32 paths (FP32 storage, FP32 Gram, FP32 recurrence): iterate relative
+    error <= 1e-5 in the 2-norm;
+  * reduced-precision Gram / storage: final risk within 1e-3 relative of the
+    oracle's risk at its own iterate.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2606_18463_gb300 import glm
+    glm.load()
+    return glm
+
+
+def _ds(G, pr, dtype="f32", **kw):
+    A = torch.from_numpy(pr.A).cuda()
+    y = torch.from_numpy(pr.y).cuda()
+    return G.Dataset(A, y, pr.loss, dtype, **kw)
+
+
+def _run(G, ds, pr, s, b, eta, lam, iters, seed, sgd=False, x0=None, **opts):
+    x = torch.zeros(pr.n, dtype=torch.float32, device="cuda") if x0 is None else \
+        torch.tensor(x0, dtype=torch.float32, device="cuda")
+    if sgd:
+        ds.sgd(x, b, eta, lam, iters, seed, **opts)
+    else:
+        ds.ca_sgd(x, s, b, eta, lam, iters, seed, **opts)
+    ds.sync()
+    return x.cpu().numpy().astype(np.float64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ----------------------------------------------------------------------------
+# Index stream: bit-exact
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [1, 3, 8192, 1_048_576, 400_000, 2**31 - 1])
+def test_indices_bit_exact(G, m):
+    for first, count, prob in [(0, 1000, 0), (12345, 777, 3), (2**40 + 5, 64, 1)]:
+        ref = oracle.sample_indices(7, prob, first, count, m)
+        host = np.zeros(count, dtype=np.int32)
+        G.glm_sample_indices(7, prob, first, count, m, host)
+        assert np.array_equal(host.astype(np.int64), ref)
+        dev = torch.zeros(count, dtype=torch.int32, device="cuda")
+        G.glm_sample_indices(7, prob, first, count, m, dev)
+        assert np.array_equal(dev.cpu().numpy().astype(np.int64), ref)
+
+
+def test_indices_empty(G):
+    G.glm_sample_indices(0, 0, 0, 0, 5, None)
+
+
+# ----------------------------------------------------------------------------
+# FP32 iterates (paper Recipe A): 1e-5 relative
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c1():
+    # logistic 8192 x 256, N(0,1/256), planted w*, lambda = 1e-4
+    return synth.logistic_planted(8192, 256, seed=0, lam=1e-4)
+
+
+def test_sgd_fp32_matches_oracle_c1(G, c1):
+    ds = _ds(G, c1)
+    x = _run(G, ds, c1, 1, 16, 0.5, 1e-4, 2048, 0, sgd=True)
+    ref = oracle.sgd(c1.A, c1.y, c1.loss, 16, 0.5, 1e-4, 2048, 0)
+    assert _rel(x, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("cluster", [0, 1, 2, 4, 16])
+def test_ca_fp32_matches_oracle_c1(G, c1, cluster):
+    ds = _ds(G, c1)
+    x = _run(G, ds, c1, 4, 16, 0.5, 1e-4, 2048, 0, gram_dtype="f32", cluster=cluster)
+    ref = oracle.sgd(c1.A, c1.y, c1.loss, 16, 0.5, 1e-4, 2048, 0)
+    assert _rel(x, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("m,n,b,s,iters,loss,lam", [
+    (97, 37, 5, 3, 31, synth.LOGISTIC, 0.0),       # ragged everything, tail block
+    (500, 8, 1, 7, 50, synth.LSQ, 1e-2),           # b = 1
+    (2000, 130, 12, 16, 200, synth.LOGISTIC, 1e-3),
+    (3000, 64, 32, 8, 100, synth.LSQ, 0.0),
+    (1024, 300, 9, 5, 47, synth.LSQ, 5e-3),
+])
+def test_ca_fp32_ragged_shapes(G, m, n, b, s, iters, loss, lam):
+    pr = synth.ragged(m, n, seed=m + n, loss=loss, lam=lam)
+    ds = _ds(G, pr)
+    eta = 0.25
+    ref = oracle.sgd(pr.A, pr.y, loss, b, eta, lam, iters, 11)
+    for cluster in (1, 4):
+        x = _run(G, ds, pr, s, b, eta, lam, iters, 11, gram_dtype="f32", cluster=cluster,
+                 chunk_outer=3)
+        assert _rel(x, ref) <= 1e-5, cluster
+    xs = _run(G, ds, pr, 1, b, eta, lam, iters, 11, sgd=True)
+    assert _rel(xs, ref) <= 1e-5
+
+
+def test_ca_fp64_recurrence_and_graph_off(G, c1):
+    ds = _ds(G, c1)
+    ref = oracle.sgd(c1.A, c1.y, c1.loss, 8, 0.5, 1e-4, 512, 3)
+    for rec in (0, 1):
+        for graph in (0, 1):
+            x = _run(G, ds, c1, 32, 8, 0.5, 1e-4, 512, 3, gram_dtype="f32",
+                     recurrence_f64=rec, use_graph=graph)
+            assert _rel(x, ref) <= 1e-5
+
+
+def test_resume_first_iter(G, c1):
+    ds = _ds(G, c1)
+    x = torch.zeros(c1.n, dtype=torch.float32, device="cuda")
+    ds.ca_sgd(x, 4, 16, 0.5, 1e-4, 1000, 5, gram_dtype="f32")
+    ds.ca_sgd(x, 4, 16, 0.5, 1e-4, 1048, 5, gram_dtype="f32", first_iter=1000)
+    ds.sync()
+    ref = oracle.sgd(c1.A, c1.y, c1.loss, 16, 0.5, 1e-4, 2048, 5)
+    assert _rel(x.cpu().numpy().astype(np.float64), ref) <= 1e-5
+
+
+def test_graph_replay_repeatable(G, c1):
+    ds = _ds(G, c1)
+    outs = []
+    for _ in range(3):
+        x = torch.zeros(c1.n, dtype=torch.float32, device="cuda")
+        ds.ca_sgd(x, 4, 16, 0.5, 1e-4, 256, 9, gram_dtype="bf16")
+        ds.sync()
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+# ----------------------------------------------------------------------------
+# Risk evaluation
+# ----------------------------------------------------------------------------
+def test_loss_matches_oracle(G, c1):
+    ds = _ds(G, c1)
+    rng = np.random.default_rng(0)
+    for lam in (0.0, 1e-4):
+        xv = rng.standard_normal(c1.n).astype(np.float32) * 0.3
+        x = torch.from_numpy(xv).cuda()
+        got = ds.loss_value(x, lam)
+        ref = oracle.loss(c1.A, c1.y, c1.loss, lam, xv.astype(np.float64))
+        assert abs(got - ref) <= 1e-6 * abs(ref)
+    pr = synth.lsq_planted(5000, 37, seed=2, lam=0.0)
+    ds2 = _ds(G, pr)
+    xv = np.linspace(-1, 1, 37).astype(np.float32)
+    got = ds2.loss_value(torch.from_numpy(xv).cuda(), 0.01)
+    ref = oracle.loss(pr.A, pr.y, pr.loss, 0.01, xv.astype(np.float64))
+    assert abs(got - ref) <= 1e-6 * abs(ref)
+
+
+# ----------------------------------------------------------------------------
+# Gram kernel against its Higham bound (paper Eq. gamma_q)
+# ----------------------------------------------------------------------------
+def _gram_bound(Y, s, b, n):
+    A = np.abs(np.asarray(Y, dtype=np.float64))
+    gam = n * 2.0**-24 / (1 - n * 2.0**-24)
+    return 2.0 * gam * oracle.gram_lower(A, s, b) + 1e-30
+
+
+def _unpack_gram(Gflat, nouter, s, b):
+    """Row-block layout -> dense strictly block-lower matrices."""
+    sb = s * b
+    out = np.zeros((nouter, sb, sb))
+    gsz = b * b * s * (s - 1) // 2
+    for g in range(nouter):
+        base = g * gsz
+        for j in range(1, s):
+            off = base + b * b * (j * (j - 1) // 2)
+            blk = Gflat[off:off + b * j * b].reshape(b, j * b)
+            out[g, j * b:(j + 1) * b, :j * b] = blk
+    return out
+
+
+@pytest.mark.parametrize("dt", ["f32", "tf32", "bf16", "f16", "e4m3"])
+@pytest.mark.parametrize("impl", [1, 0])
+@pytest.mark.parametrize("nouter,s,b,n", [(3, 4, 16, 100), (2, 16, 64, 512), (1, 3, 130, 70)])
+def test_gram_lower_bound(G, dt, impl, nouter, s, b, n):
+    rng = np.random.default_rng(s * 1000 + b + n)
+    sb = s * b
+    ld = ((n + 63) // 64) * 64
+    Yf = rng.standard_normal((nouter * sb, n)).astype(np.float32)
+    rs = None
+    if dt == "f32":
+        vals = Yf.astype(np.float64)
+        dev = np.zeros((nouter * sb, ld), np.float32); dev[:, :n] = Yf
+        Yd = torch.from_numpy(dev).cuda()
+    elif dt == "tf32":
+        vals = oracle.round_tf32(Yf).astype(np.float64)
+        dev = np.zeros((nouter * sb, ld), np.float32); dev[:, :n] = vals
+        Yd = torch.from_numpy(dev).cuda()
+    elif dt == "bf16":
+        vals = oracle.round_bf16(Yf).astype(np.float64)
+        dev = np.zeros((nouter * sb, ld), np.float32); dev[:, :n] = vals
+        Yd = torch.from_numpy(dev).to(torch.bfloat16).cuda()
+    elif dt == "f16":
+        vals = oracle.round_f16(Yf).astype(np.float64)
+        dev = np.zeros((nouter * sb, ld), np.float32); dev[:, :n] = vals
+        Yd = torch.from_numpy(dev).to(torch.float16).cuda()
+    else:
+        rho = oracle.fp8_row_scales(Yf)
+        q = oracle.round_e4m3(Yf / rho[:, None])
+        vals = q * rho[:, None]
+        dev = np.zeros((nouter * sb, ld), np.float32); dev[:, :n] = q
+        Yd = torch.from_numpy(dev).to(torch.float8_e4m3fn).view(torch.uint8).cuda()
+        rs = torch.from_numpy(rho.astype(np.float32)).cuda()
+    gsz = b * b * s * (s - 1) // 2
+    Gd = torch.full((nouter * gsz,), float("nan"), dtype=torch.float32, device="cuda")
+    G.glm_gram_lower(Yd, G.DTYPES[dt], nouter, s, b, n, ld, rs, Gd, impl)
+    torch.cuda.synchronize()
+    got = _unpack_gram(Gd.cpu().numpy().astype(np.float64), nouter, s, b)
+    for g in range(nouter):
+        Yg = vals[g * sb:(g + 1) * sb]
+        ref = oracle.gram_lower(Yg, s, b)
+        bound = _gram_bound(Yg, s, b, n)
+        err = np.abs(got[g] - ref)
+        assert np.all(err <= bound), (dt, impl, float(np.max(err - bound)))
+
+
+# ----------------------------------------------------------------------------
+# Reduced precision: final risk within 1e-3 of the oracle's
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,gram", [("f32", "tf32"), ("f32", "bf16"), ("f32", "f16"),
+                                          ("bf16", "bf16"), ("f16", "f16"), ("bf16", "e4m3")])
+def test_low_precision_final_loss(G, c1, storage, gram):
+    ds = _ds(G, c1, storage, fp8_copy=(gram == "e4m3"))
+    x = _run(G, ds, c1, 4, 16, 0.5, 1e-4, 2048, 0, gram_dtype=gram)
+    ref = oracle.sgd(c1.A, c1.y, c1.loss, 16, 0.5, 1e-4, 2048, 0)
+    f = oracle.loss(c1.A, c1.y, c1.loss, 1e-4, x)
+    fr = oracle.loss(c1.A, c1.y, c1.loss, 1e-4, ref)
+    tol = 1e-3 if gram != "e4m3" else 5e-3
+    assert abs(f - fr) <= tol * fr, (storage, gram, f, fr)
+
+
+# ----------------------------------------------------------------------------
+# Errors
+# ----------------------------------------------------------------------------
+def test_argument_errors(G, c1):
+    ds = _ds(G, c1)
+    x = torch.zeros(c1.n, dtype=torch.float32, device="cuda")
+    with pytest.raises(G.GlmError) as e:
+        ds.ca_sgd(x, 0, 16, 0.5, 0.0, 10, 0)
+    assert e.value.code == G.GLM_EINVAL
+    with pytest.raises(G.GlmError) as e:
+        ds.ca_sgd(x, 4, 16, 0.5, 3.0, 10, 0)  # eta*lambda >= 1
+    assert e.value.code == G.GLM_EINVAL
+    with pytest.raises(G.GlmError) as e:
+        ds.ca_sgd(x, 4, 16, -1.0, 0.0, 10, 0)
+    assert e.value.code == G.GLM_EINVAL
+    with pytest.raises(G.GlmError) as e:
+        ds.ca_sgd(x, 4, 16, 0.5, 0.0, 10, 0, gram_dtype="e4m3")  # no FP8 copy
+    assert e.value.code == G.GLM_EINVAL
+    bad = c1.y.copy()
+    bad[5] = 0.5
+    with pytest.raises(G.GlmError) as e:
+        G.Dataset(torch.from_numpy(c1.A).cuda(), torch.from_numpy(bad).cuda(), G.GLM_LOGISTIC)
+    assert e.value.code == G.GLM_EINVAL
+
+
+def test_nonfinite_detected(G):
+    pr = synth.lsq_planted(4096, 64, seed=1, var=100.0)
+    ds = _ds(G, pr)
+    x = torch.zeros(pr.n, dtype=torch.float32, device="cuda")
+    ds.ca_sgd(x, 4, 8, 0.9, 0.0, 4000, 0, gram_dtype="f32")  # diverges
+    assert G.glm_sync(ds.h) == G.GLM_ENONFINITE
+    assert G.glm_sync(ds.h) == G.GLM_OK  # flag cleared
