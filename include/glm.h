@@ -133,9 +133,33 @@ typedef struct {
   int64_t chunk_outer;/* outer iterations staged per chunk; 0 = automatic.   */
   int gram_impl;      /* 0 (default) automatic, 1 SIMT FP32 kernel,
                          2 tcgen05 tensor-core kernel.                        */
+  int timing;         /* 1: record CUDA events around every kernel of the run
+                         (read back with glm_kernel_times).  Default 0.       */
 } glm_ca_opts;
 
 void glm_ca_opts_default(glm_ca_opts *o);
+
+/* What a run with these arguments will do (no work is enqueued). */
+typedef struct {
+  int64_t chunk_outer;  /* outer iterations staged per chunk                  */
+  int64_t chunks;       /* number of chunks                                   */
+  int64_t launches;     /* kernels launched by the run                        */
+  int cluster;          /* CTAs in the chain cluster                          */
+  int gram_impl;        /* 1 SIMT, 2 tcgen05                                  */
+  int gram_dtype, gemv_dtype, recurrence_f64;
+} glm_run_plan;
+
+int glm_ca_plan(glm_handle h, int s, int64_t b, float eta, float lambda,
+                int64_t iters, const glm_ca_opts *opts, glm_run_plan *out);
+
+/*
+ * Per-kernel device time of the most recent run made with opts.timing = 1,
+ * from CUDA events recorded on the handle's stream (inside the captured
+ * graph when graphs are used).  ms[0..2] = summed milliseconds of the
+ * gather, Gram and chain kernels; launches[0..2] = their launch counts.
+ * Blocks until that run has finished.
+ */
+int glm_kernel_times(glm_handle h, double *ms, int64_t *launches);
 
 /*
  * Plain mini-batch SGD (paper Sec. 2.1 / Sec. 3.1) in FP32 with FP32 master

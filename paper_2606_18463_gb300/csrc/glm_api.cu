@@ -51,7 +51,7 @@ bool RunKey::operator==(const RunKey &o) const {
          kahan == o.kahan && cluster == o.cluster && gram_impl == o.gram_impl &&
          sgd == o.sgd && b == o.b && iters == o.iters && first_iter == o.first_iter &&
          chunk == o.chunk && seed == o.seed && problem == o.problem && eta == o.eta &&
-         lambda == o.lambda && x == o.x;
+         lambda == o.lambda && x == o.x && timing == o.timing;
 }
 
 int loss_partials_needed();
@@ -70,6 +70,7 @@ bool is_device_ptr(const void *p) {
 void free_handle(Handle *h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
   h->ygram.release();
   h->ygemv.release();
   h->ylab.release();
@@ -92,7 +93,8 @@ struct RunPlan {
   int s = 1;
   int64_t b = 1, iters = 0, H = 0, chunk = 1;
   int gram_dt = GLM_F32, gemv_dt = GLM_F32, rec64 = 0, kahan = 1, cluster = 1;
-  int gram_impl = 1, sgd = 0, use_graph = 1;
+  int gram_impl = 1, sgd = 0, use_graph = 1, timing = 0;
+  int64_t chunks = 0, launches = 0;
   int64_t ld_gram = 0, ld_gemv = 0;  // 0 ld_gemv: GEMV reads the Gram copy
   float eta = 0.f, lambda = 0.f, alpha = 0.f;
   double c = 1.0;
@@ -133,6 +135,7 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   p.sgd = sgd ? 1 : 0;
   p.kahan = o->kahan ? 1 : 0;
   p.use_graph = o->use_graph ? 1 : 0;
+  p.timing = o->timing ? 1 : 0;
   // precision slots
   int gdt = o->gram_dtype < 0 ? h->dtype : o->gram_dtype;
   if (sgd) gdt = (o->gram_dtype < 0) ? GLM_F32 : o->gram_dtype;
@@ -157,7 +160,7 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   // chunking
   p.H = (iters + s - 1) / s;
   const int64_t sb = (int64_t)s * b;
-  const int64_t gsz = b * b * (int64_t)s * (s - 1) / 2;
+  const int64_t gsz = gram_size(s, b);
   const int64_t per_outer = sb * (p.ld_gram * elem_bytes(gdt) +
                                   (p.ld_gemv ? p.ld_gemv * elem_bytes(vdt) : 0) + 8) +
                             gsz * 4;
@@ -186,14 +189,30 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   }
   if (C > cmax) C = cmax;
   if (C < 1 || C > 16) return set_error(GLM_EINVAL, "cluster must be in [1, 16]");
+  while (C > 1 && !chain_cluster_ok(C, b)) C /= 2;
   p.cluster = C;
+  p.chunks = (p.H + p.chunk - 1) / p.chunk;
+  p.launches = p.chunks * (s > 1 ? 3 : 2);
+  return GLM_OK;
+}
+
+// Record timing event (chunk c, kernel k, edge e) when the run is timed.
+int tmark(Handle *h, const RunPlan &p, cudaStream_t st, int64_t c, int k, int e) {
+  if (!p.timing) return GLM_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  GLM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  cudaEvent_t ev = h->tev[(size_t)(c * 6 + k * 2 + e)];
+  if (cs == cudaStreamCaptureStatusActive)
+    GLM_CUDA_TRY(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+  else
+    GLM_CUDA_TRY(cudaEventRecord(ev, st));
   return GLM_OK;
 }
 
 int ensure_scratch(Handle *h, const RunPlan &p, bool &realloc) {
   const int64_t sb = (int64_t)p.s * p.b;
   const int64_t rows = p.chunk * sb;
-  const int64_t gsz = p.b * p.b * (int64_t)p.s * (p.s - 1) / 2;
+  const int64_t gsz = gram_size(p.s, p.b);
   void *before[5] = {h->ygram.ptr, h->ygemv.ptr, h->ylab.ptr, h->yscale.ptr, h->gbuf.ptr};
   GLM_TRY(h->ygram.ensure((size_t)rows * p.ld_gram * elem_bytes(p.gram_dt)));
   if (p.ld_gemv) GLM_TRY(h->ygemv.ensure((size_t)rows * p.ld_gemv * elem_bytes(p.gemv_dt)));
@@ -208,6 +227,15 @@ int ensure_scratch(Handle *h, const RunPlan &p, bool &realloc) {
 // Enqueue a whole run on stream st.
 int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
   const int64_t sb = (int64_t)p.s * p.b;
+  if (p.timing) {
+    while ((int64_t)h->tev.size() < p.chunks * 6) {
+      cudaEvent_t e;
+      GLM_CUDA_TRY(cudaEventCreate(&e));
+      h->tev.push_back(e);
+    }
+    h->tev_chunks = p.chunks;
+    h->tev_valid = p.s > 1 ? 7 : 5;  // bit k: kernel k was timed
+  }
   ChainArgs ca;
   memset(&ca, 0, sizeof(ca));
   ca.dt = p.gemv_dt;
@@ -263,7 +291,10 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
     }
     ga.ylab = static_cast<float *>(h->ylab.ptr);
     ga.rscale = static_cast<float *>(h->yscale.ptr);
+    const int64_t ci = h0 / p.chunk;
+    GLM_TRY(tmark(h, p, st, ci, 0, 0));
     GLM_TRY(launch_gather(ga, st));
+    GLM_TRY(tmark(h, p, st, ci, 0, 1));
     if (p.s > 1) {
       GramArgs gr;
       gr.Y = h->ygram.ptr;
@@ -276,12 +307,16 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
       gr.b = p.b;
       gr.n = h->n;
       gr.G = static_cast<float *>(h->gbuf.ptr);
+      GLM_TRY(tmark(h, p, st, ci, 1, 0));
       if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, st));
       else GLM_TRY(launch_gram_simt(gr, st));
+      GLM_TRY(tmark(h, p, st, ci, 1, 1));
     }
     ca.nouter = (int)nout;
     ca.s_last = s_last;
+    GLM_TRY(tmark(h, p, st, ci, 2, 0));
     GLM_TRY(launch_chain(ca, st));
+    GLM_TRY(tmark(h, p, st, ci, 2, 1));
     (void)sb;
   }
   return GLM_OK;
@@ -300,7 +335,7 @@ int run_common(Handle *h, int s, int64_t b, float eta, float lambda, int64_t ite
   key.kahan = p.kahan; key.cluster = p.cluster; key.gram_impl = p.gram_impl; key.sgd = p.sgd;
   key.b = p.b; key.iters = p.iters; key.first_iter = p.first_iter; key.chunk = p.chunk;
   key.seed = p.seed; key.problem = p.problem; key.eta = p.eta; key.lambda = p.lambda;
-  key.x = p.x;
+  key.x = p.x; key.timing = p.timing;
   if (realloc && h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -370,6 +405,7 @@ void glm_ca_opts_default(glm_ca_opts *o) {
   o->cluster = 0;
   o->chunk_outer = 0;
   o->gram_impl = 0;
+  o->timing = 0;
 }
 
 int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss, int dtype,
@@ -550,6 +586,46 @@ int glm_ca_sgd_run_ex(glm_handle hh, int s, int64_t b, float eta, float lambda, 
 int glm_ca_sgd_run(glm_handle h, int s, int64_t b, float eta, float lambda, int64_t iters,
                    uint64_t seed, float *x) {
   return glm_ca_sgd_run_ex(h, s, b, eta, lambda, iters, seed, x, nullptr);
+}
+
+int glm_ca_plan(glm_handle hh, int s, int64_t b, float eta, float lambda, int64_t iters,
+                const glm_ca_opts *opts, glm_run_plan *out) {
+  g_last_error.clear();
+  if (!out) return set_error(GLM_EINVAL, "out is NULL");
+  float dummy = 0.f;
+  RunPlan p;
+  GLM_TRY(resolve(reinterpret_cast<Handle *>(hh), s, b, eta, lambda, iters, 0, &dummy, opts,
+                  false, p));
+  out->chunk_outer = p.chunk;
+  out->chunks = iters > 0 ? p.chunks : 0;
+  out->launches = iters > 0 ? p.launches : 0;
+  out->cluster = p.cluster;
+  out->gram_impl = p.gram_impl;
+  out->gram_dtype = p.gram_dt;
+  out->gemv_dtype = p.gemv_dt;
+  out->recurrence_f64 = p.rec64;
+  return GLM_OK;
+}
+
+int glm_kernel_times(glm_handle hh, double *ms, int64_t *launches) {
+  g_last_error.clear();
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h || !ms || !launches) return set_error(GLM_EINVAL, "null argument");
+  if (!h->tev_valid) return set_error(GLM_EINVAL, "no run with opts.timing = 1 yet");
+  GLM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+    if (!(h->tev_valid & (1 << k))) continue;
+    for (int64_t c = 0; c < h->tev_chunks; ++c) {
+      float t = 0.f;
+      GLM_CUDA_TRY(cudaEventElapsedTime(&t, h->tev[(size_t)(c * 6 + k * 2)],
+                                        h->tev[(size_t)(c * 6 + k * 2 + 1)]));
+      ms[k] += t;
+      launches[k] += 1;
+    }
+  }
+  return GLM_OK;
 }
 
 int glm_loss(glm_handle hh, const float *x, float lambda, double *out) {

@@ -173,6 +173,94 @@ __host__ __device__ inline int64_t round_up(int64_t v, int64_t a) {
 }
 
 // ---------------------------------------------------------------------------
+// Packed strictly block-lower Gram layout (per outer iteration): block row j
+// (1 <= j < s) holds b rows of j*b values G[j b + l][0 .. j b), row stride
+// gram_ld(j, b) = round_up(j b, 4) floats (16-byte aligned rows), starting
+// at float offset gram_off(j, b); gram_size(s, b) floats per iteration.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int64_t gram_ld(int64_t j, int64_t b) { return round_up(j * b, 4); }
+
+__host__ __device__ inline int64_t gram_off(int64_t j, int64_t b) {
+  int64_t o = 0;
+  for (int64_t t = 1; t < j; ++t) o += b * gram_ld(t, b);
+  return o;
+}
+
+__host__ __device__ inline int64_t gram_size(int64_t s, int64_t b) { return gram_off(s, b); }
+
+// ---------------------------------------------------------------------------
+// Inline PTX: mbarriers, cluster-scope asynchronous stores, async copies
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init_cluster() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+               ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after `budget` SM clock cycles and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  long long budget) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+// Address of the same shared-memory location in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+// Store to a (possibly remote) cluster shared address and signal `bytes`
+// on the destination CTA's mbarrier.
+__device__ __forceinline__ void st_async(uint32_t raddr, float v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               ::"r"(raddr), "r"(__float_as_uint(v)), "r"(rbar) : "memory");
+}
+
+__device__ __forceinline__ void st_async(uint32_t raddr, double v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+               ::"r"(raddr), "l"(__double_as_longlong(v)), "r"(rbar) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Losses (paper Sec. 2.1): u = dL/dr and L itself
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -221,7 +309,7 @@ struct DevBuf {
 
 struct RunKey {
   int s = 0, gram_dt = 0, gemv_dt = 0, rec64 = 0, kahan = 0, cluster = 0,
-      gram_impl = 0, sgd = 0;
+      gram_impl = 0, sgd = 0, timing = 0;
   int64_t b = 0, iters = 0, first_iter = 0, chunk = 0;
   uint64_t seed = 0;
   uint32_t problem = 0;
@@ -249,6 +337,10 @@ struct Handle {
   // captured run graph
   cudaGraphExec_t graph = nullptr;
   RunKey graph_key;
+  // per-kernel timing events of the last timed run: [chunk][kernel][start,end]
+  std::vector<cudaEvent_t> tev;
+  int64_t tev_chunks = 0;
+  int tev_valid = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -293,6 +385,7 @@ struct ChainArgs {
 };
 int launch_chain(const ChainArgs &a, cudaStream_t st);
 int chain_max_cluster(const ChainArgs &a);
+bool chain_cluster_ok(int C, int64_t b);
 
 int launch_loss(Handle *h, const float *x, float lambda, cudaStream_t st);
 int launch_sample(uint64_t seed, uint64_t problem, int64_t first, int64_t count,

@@ -93,14 +93,13 @@ k_gram_simt(GramArgs a) {
     }
   }
   // epilogue: strictly block-lower entries into the row-block layout
-  const int64_t bb = a.b * a.b;
-  float *Gg = a.G + g * (bb * a.s * (a.s - 1) / 2);
+  float *Gg = a.G + g * gram_size(a.s, a.b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t rho = r0 + ty * 4 + i;
     if (rho >= rows_g) continue;
     const int64_t j = rho / a.b, l = rho - j * a.b;
-    float *grow = Gg + bb * (j * (j - 1) / 2) + l * (j * a.b);
+    float *grow = Gg + gram_off(j, a.b) + l * gram_ld(j, a.b);
     const float sr = a.rs ? a.rs[g * sb + rho] : 1.f;
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {

@@ -35,7 +35,8 @@ EXPORTED = [
     "glm_last_error", "glm_version", "glm_create_opts_default", "glm_create",
     "glm_create_ex", "glm_destroy", "glm_shape", "glm_stream", "glm_sync",
     "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_ca_sgd_run",
-    "glm_ca_sgd_run_ex", "glm_loss", "glm_sample_indices", "glm_gram_lower",
+    "glm_ca_sgd_run_ex", "glm_ca_plan", "glm_kernel_times", "glm_loss",
+    "glm_sample_indices", "glm_gram_lower",
     "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
     "glm_batch_choice", "glm_batch_destroy",
 ]
@@ -58,7 +59,15 @@ class glm_ca_opts(ctypes.Structure):
                 ("recurrence_f64", ctypes.c_int), ("kahan", ctypes.c_int),
                 ("first_iter", ctypes.c_int64), ("problem", ctypes.c_uint32),
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("chunk_outer", ctypes.c_int64), ("gram_impl", ctypes.c_int)]
+                ("chunk_outer", ctypes.c_int64), ("gram_impl", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+class glm_run_plan(ctypes.Structure):
+    _fields_ = [("chunk_outer", ctypes.c_int64), ("chunks", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("cluster", ctypes.c_int),
+                ("gram_impl", ctypes.c_int), ("gram_dtype", ctypes.c_int),
+                ("gemv_dtype", ctypes.c_int), ("recurrence_f64", ctypes.c_int)]
 
 
 class glm_problem_desc(ctypes.Structure):
@@ -108,6 +117,10 @@ def load():
             "glm_ca_sgd_run": ([vp, i32, i64, f32, f32, i64, u64, vp], i32),
             "glm_ca_sgd_run_ex": ([vp, i32, i64, f32, f32, i64, u64, vp,
                                    ctypes.POINTER(glm_ca_opts)], i32),
+            "glm_ca_plan": ([vp, i32, i64, f32, f32, i64, ctypes.POINTER(glm_ca_opts),
+                             ctypes.POINTER(glm_run_plan)], i32),
+            "glm_kernel_times": ([vp, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(i64)], i32),
             "glm_loss": ([vp, vp, f32, ctypes.POINTER(ctypes.c_double)], i32),
             "glm_sample_indices": ([u64, ctypes.c_uint32, i64, i64, i64, vp], i32),
             "glm_gram_lower": ([vp, i32, i64, i32, i64, i64, i64, vp, vp, i32, vp], i32),
@@ -222,6 +235,21 @@ def glm_gram_lower(Y, dtype, nouter, s, b, n, ld, row_scale, G, impl=0, stream=N
 
 def glm_stream(h) -> int:
     return load().glm_stream(h)
+
+
+def glm_ca_plan(h, s, b, eta, lam, iters, opts=None) -> glm_run_plan:
+    out = glm_run_plan()
+    _check(load().glm_ca_plan(h, s, b, eta, lam, iters,
+                              ctypes.byref(opts) if opts is not None else None,
+                              ctypes.byref(out)))
+    return out
+
+
+def glm_kernel_times(h):
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(load().glm_kernel_times(h, ms, n))
+    return list(ms), list(n)
 
 
 # ---- convenience wrapper -------------------------------------------------------

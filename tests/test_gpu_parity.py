@@ -173,14 +173,20 @@ def _unpack_gram(Gflat, nouter, s, b):
     """Row-block layout -> dense strictly block-lower matrices."""
     sb = s * b
     out = np.zeros((nouter, sb, sb))
-    gsz = b * b * s * (s - 1) // 2
+    lds = [((j * b + 3) // 4) * 4 for j in range(s)]
+    offs = [b * sum(lds[1:j]) for j in range(s + 1)]
+    gsz = offs[s]
     for g in range(nouter):
         base = g * gsz
         for j in range(1, s):
-            off = base + b * b * (j * (j - 1) // 2)
-            blk = Gflat[off:off + b * j * b].reshape(b, j * b)
+            off = base + offs[j]
+            blk = Gflat[off:off + b * lds[j]].reshape(b, lds[j])[:, :j * b]
             out[g, j * b:(j + 1) * b, :j * b] = blk
     return out
+
+
+def _gram_size(s, b):
+    return b * sum(((j * b + 3) // 4) * 4 for j in range(1, s))
 
 
 @pytest.mark.parametrize("dt", ["f32", "tf32", "bf16", "f16", "e4m3"])
@@ -215,7 +221,7 @@ def test_gram_lower_bound(G, dt, impl, nouter, s, b, n):
         dev = np.zeros((nouter * sb, ld), np.float32); dev[:, :n] = q
         Yd = torch.from_numpy(dev).to(torch.float8_e4m3fn).view(torch.uint8).cuda()
         rs = torch.from_numpy(rho.astype(np.float32)).cuda()
-    gsz = b * b * s * (s - 1) // 2
+    gsz = _gram_size(s, b)
     Gd = torch.full((nouter * gsz,), float("nan"), dtype=torch.float32, device="cuda")
     G.glm_gram_lower(Yd, G.DTYPES[dt], nouter, s, b, n, ld, rs, Gd, impl)
     torch.cuda.synchronize()
