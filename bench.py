@@ -43,7 +43,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--s", type=int, default=16)
+    ap.add_argument("--s", type=int, default=8)
     ap.add_argument("--gram", default="bf16", choices=["f32", "tf32", "bf16", "f16"])
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true",
@@ -308,6 +308,28 @@ def main():
                     "cluster": plan.cluster, "gram_impl": plan.gram_impl}}
 
     if not args.no_extras:
+        # ---- the other s of the workload, one timed run each ------------------
+        sweep = {}
+        with torch.cuda.stream(stream):
+            for s2 in (8, 16, 32):
+                o2 = dict(opts, timing=0)
+
+                def run2():
+                    x.zero_()
+                    ds.ca_sgd(x, s2, b, w["eta"], w["lam"], T, seed, **o2)
+                run2()
+                stream.synchronize()
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                run2()
+                g1.record(stream)
+                stream.synchronize()
+                ms2 = g0.elapsed_time(g1)
+                sweep[f"s={s2}"] = {"samples_per_s": T * b / (ms2 / 1e3), "ms_per_run": ms2,
+                                    "recurrence": "f64" if s2 >= 32 else "f32"}
+        out["s_sweep"] = sweep
+
         # ---- FP32 plain-SGD GPU baseline (same data, same index stream) -------
         with torch.cuda.stream(stream):
             xs = torch.zeros(pr.n, dtype=torch.float32, device="cuda")

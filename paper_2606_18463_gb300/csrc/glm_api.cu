@@ -71,11 +71,18 @@ void free_handle(Handle *h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
-  h->ygram.release();
-  h->ygemv.release();
-  h->ylab.release();
-  h->yscale.release();
-  h->gbuf.release();
+  for (int k = 0; k < 2; ++k) {
+    h->ygram[k].release();
+    h->ygemv[k].release();
+    h->ylab[k].release();
+    h->yscale[k].release();
+    h->gbuf[k].release();
+    if (h->ev_bulk[k]) cudaEventDestroy(h->ev_bulk[k]);
+    if (h->ev_chain[k]) cudaEventDestroy(h->ev_chain[k]);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   cudaFree(h->A);
   cudaFree(h->y);
   cudaFree(h->colscale);
@@ -150,7 +157,7 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   p.gram_dt = gdt;
   p.gemv_dt = vdt;
   p.rec64 = o->recurrence_f64 < 0 ? (s >= 32 ? 1 : 0) : (o->recurrence_f64 ? 1 : 0);
-  p.ld_gram = round_up(h->n, 64);
+  p.ld_gram = round_up(h->n, gdt == GLM_E4M3 ? 128 : 64);
   p.ld_gemv = (vdt == gdt) ? 0 : round_up(h->n, 64);
   // Gram implementation
   if (o->gram_impl == 2 && !gram_tc_supported(gdt, p.ld_gram))
@@ -179,16 +186,21 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   probe.b = b;
   probe.s = s;
   probe.rec64 = p.rec64;
+  probe.prefetch = 1;
   const int cmax = chain_max_cluster(probe);
   if (cmax < 1)
     return set_error(GLM_EUNSUPPORTED, "s*b too large for the on-chip recurrence state");
   int C = o->cluster;
   if (C <= 0) {
+    // widest cluster that keeps >= 4 rows of each block and >= 32 columns
+    // per CTA (16-byte exchanges, full-width slice rows); measured best on
+    // the 2^20 x 512 and 8192 x 256 workloads
     C = 1;
-    while (C < 16 && (int64_t)C * 64 < h->n) C *= 2;
+    while (C < 16 && b / (2 * C) >= 4 && h->n / (2 * C) >= 32) C *= 2;
   }
   if (C > cmax) C = cmax;
-  if (C < 1 || C > 16) return set_error(GLM_EINVAL, "cluster must be in [1, 16]");
+  if (C < 1 || C > 16 || (C & (C - 1)))
+    return set_error(GLM_EINVAL, "cluster must be a power of two in [1, 16]");
   while (C > 1 && !chain_cluster_ok(C, b)) C /= 2;
   p.cluster = C;
   p.chunks = (p.H + p.chunk - 1) / p.chunk;
@@ -213,14 +225,36 @@ int ensure_scratch(Handle *h, const RunPlan &p, bool &realloc) {
   const int64_t sb = (int64_t)p.s * p.b;
   const int64_t rows = p.chunk * sb;
   const int64_t gsz = gram_size(p.s, p.b);
-  void *before[5] = {h->ygram.ptr, h->ygemv.ptr, h->ylab.ptr, h->yscale.ptr, h->gbuf.ptr};
-  GLM_TRY(h->ygram.ensure((size_t)rows * p.ld_gram * elem_bytes(p.gram_dt)));
-  if (p.ld_gemv) GLM_TRY(h->ygemv.ensure((size_t)rows * p.ld_gemv * elem_bytes(p.gemv_dt)));
-  GLM_TRY(h->ylab.ensure((size_t)rows * 4));
-  GLM_TRY(h->yscale.ensure((size_t)rows * 4));
-  GLM_TRY(h->gbuf.ensure((size_t)std::max<int64_t>(1, p.chunk * gsz) * 4));
-  void *after[5] = {h->ygram.ptr, h->ygemv.ptr, h->ylab.ptr, h->yscale.ptr, h->gbuf.ptr};
+  const int nb = p.chunks > 1 ? 2 : 1;
+  void *before[10], *after[10];
+  for (int k = 0; k < 2; ++k) {
+    before[5 * k] = h->ygram[k].ptr; before[5 * k + 1] = h->ygemv[k].ptr;
+    before[5 * k + 2] = h->ylab[k].ptr; before[5 * k + 3] = h->yscale[k].ptr;
+    before[5 * k + 4] = h->gbuf[k].ptr;
+  }
+  for (int k = 0; k < nb; ++k) {
+    GLM_TRY(h->ygram[k].ensure((size_t)rows * p.ld_gram * elem_bytes(p.gram_dt)));
+    if (p.ld_gemv)
+      GLM_TRY(h->ygemv[k].ensure((size_t)rows * p.ld_gemv * elem_bytes(p.gemv_dt)));
+    GLM_TRY(h->ylab[k].ensure((size_t)p.chunk * round_up(sb, 4) * 4));
+    GLM_TRY(h->yscale[k].ensure((size_t)rows * 4));
+    GLM_TRY(h->gbuf[k].ensure((size_t)std::max<int64_t>(1, p.chunk * gsz) * 4));
+  }
+  for (int k = 0; k < 2; ++k) {
+    after[5 * k] = h->ygram[k].ptr; after[5 * k + 1] = h->ygemv[k].ptr;
+    after[5 * k + 2] = h->ylab[k].ptr; after[5 * k + 3] = h->yscale[k].ptr;
+    after[5 * k + 4] = h->gbuf[k].ptr;
+  }
   realloc = memcmp(before, after, sizeof(before)) != 0;
+  if (!h->side) {
+    GLM_CUDA_TRY(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    GLM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    GLM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    for (int k = 0; k < 2; ++k) {
+      GLM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_bulk[k], cudaEventDisableTiming));
+      GLM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_chain[k], cudaEventDisableTiming));
+    }
+  }
   return GLM_OK;
 }
 
@@ -239,10 +273,7 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
   ChainArgs ca;
   memset(&ca, 0, sizeof(ca));
   ca.dt = p.gemv_dt;
-  ca.Y = p.ld_gemv ? h->ygemv.ptr : h->ygram.ptr;
   ca.ldy = p.ld_gemv ? p.ld_gemv : p.ld_gram;
-  ca.ylab = static_cast<const float *>(h->ylab.ptr);
-  ca.G = static_cast<const float *>(h->gbuf.ptr);
   ca.x = p.x;
   ca.flag = h->dflag;
   ca.n = h->n;
@@ -253,13 +284,26 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
   ca.rec64 = p.rec64;
   ca.kahan = p.kahan;
   ca.cluster = p.cluster;
+  ca.sbp = round_up(sb, 4);
+  ca.prefetch = 1;
   double cp = 1.0;
   for (int j = 0; j <= p.s; ++j) {
     ca.cpow[j] = cp;
     ca.cinv[j] = 1.0 / cp;
     cp *= p.c;
   }
+  // the x-independent work (gather, Gram) runs on the side stream, one chunk
+  // ahead of the chain on `st`; chunk buffers alternate
+  const int nb = p.chunks > 1 ? 2 : 1;
+  cudaStream_t side = h->side;
+  GLM_CUDA_TRY(cudaEventRecord(h->ev_fork, st));
+  GLM_CUDA_TRY(cudaStreamWaitEvent(side, h->ev_fork, 0));
   for (int64_t h0 = 0; h0 < p.H; h0 += p.chunk) {
+    const int buf = (int)((h0 / p.chunk) % nb);
+    if (h0 / p.chunk >= nb) GLM_CUDA_TRY(cudaStreamWaitEvent(side, h->ev_chain[buf], 0));
+    ca.Y = p.ld_gemv ? h->ygemv[buf].ptr : h->ygram[buf].ptr;
+    ca.ylab = static_cast<const float *>(h->ylab[buf].ptr);
+    ca.G = static_cast<const float *>(h->gbuf[buf].ptr);
     const int64_t nout = std::min<int64_t>(p.chunk, p.H - h0);
     const int64_t it0 = h0 * p.s;                          // first iteration of chunk
     const int64_t it1 = std::min<int64_t>(p.iters, (h0 + nout) * p.s);
@@ -281,44 +325,51 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
     ga.q0 = (uint64_t)((p.first_iter + it0) * p.b);
     ga.seed = p.seed;
     ga.problem = p.problem;
-    ga.out1 = h->ygram.ptr;
+    ga.out1 = h->ygram[buf].ptr;
     ga.dt1 = p.gram_dt;
     ga.ld1 = p.ld_gram;
     if (p.ld_gemv) {
-      ga.out2 = h->ygemv.ptr;
+      ga.out2 = h->ygemv[buf].ptr;
       ga.dt2 = p.gemv_dt;
       ga.ld2 = p.ld_gemv;
     }
-    ga.ylab = static_cast<float *>(h->ylab.ptr);
-    ga.rscale = static_cast<float *>(h->yscale.ptr);
+    ga.ylab = static_cast<float *>(h->ylab[buf].ptr);
+    ga.rscale = static_cast<float *>(h->yscale[buf].ptr);
+    ga.lab_sb = sb;
+    ga.lab_sbp = round_up(sb, 4);
     const int64_t ci = h0 / p.chunk;
-    GLM_TRY(tmark(h, p, st, ci, 0, 0));
-    GLM_TRY(launch_gather(ga, st));
-    GLM_TRY(tmark(h, p, st, ci, 0, 1));
+    GLM_TRY(tmark(h, p, side, ci, 0, 0));
+    GLM_TRY(launch_gather(ga, side));
+    GLM_TRY(tmark(h, p, side, ci, 0, 1));
     if (p.s > 1) {
       GramArgs gr;
-      gr.Y = h->ygram.ptr;
+      gr.Y = h->ygram[buf].ptr;
       gr.dt = p.gram_dt;
       gr.ld = p.ld_gram;
-      gr.rs = p.gram_dt == GLM_E4M3 ? static_cast<const float *>(h->yscale.ptr) : nullptr;
+      gr.rs = p.gram_dt == GLM_E4M3 ? static_cast<const float *>(h->yscale[buf].ptr) : nullptr;
       gr.nouter = nout;
       gr.rows = rows;
       gr.s = p.s;
       gr.b = p.b;
       gr.n = h->n;
-      gr.G = static_cast<float *>(h->gbuf.ptr);
-      GLM_TRY(tmark(h, p, st, ci, 1, 0));
-      if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, st));
-      else GLM_TRY(launch_gram_simt(gr, st));
-      GLM_TRY(tmark(h, p, st, ci, 1, 1));
+      gr.G = static_cast<float *>(h->gbuf[buf].ptr);
+      gr.flag = h->dflag;
+      GLM_TRY(tmark(h, p, side, ci, 1, 0));
+      if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, side));
+      else GLM_TRY(launch_gram_simt(gr, side));
+      GLM_TRY(tmark(h, p, side, ci, 1, 1));
     }
+    GLM_CUDA_TRY(cudaEventRecord(h->ev_bulk[buf], side));
+    GLM_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bulk[buf], 0));
     ca.nouter = (int)nout;
     ca.s_last = s_last;
     GLM_TRY(tmark(h, p, st, ci, 2, 0));
     GLM_TRY(launch_chain(ca, st));
     GLM_TRY(tmark(h, p, st, ci, 2, 1));
-    (void)sb;
+    GLM_CUDA_TRY(cudaEventRecord(h->ev_chain[buf], st));
   }
+  GLM_CUDA_TRY(cudaEventRecord(h->ev_join, side));
+  GLM_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0));
   return GLM_OK;
 }
 
@@ -684,6 +735,7 @@ int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b, i
   a.b = b;
   a.n = n;
   a.G = G;
+  a.flag = nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (impl == 0) impl = gram_tc_supported(dtype, ld) ? 2 : 1;
   if (impl == 2) {

@@ -218,12 +218,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after `budget` SM clock cycles and returns false.
+// Non-suspending probe of a phase (a thread parked inside try_wait can take
+// microseconds to resume, which dominates latency-bound exchanges).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Bounded spin: gives up after `budget` SM clock cycles and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   long long budget) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  while (!mbar_test_wait(bar, parity)) {
     if (clock64() - t0 > budget) return false;
   }
   return true;
@@ -248,6 +260,27 @@ __device__ __forceinline__ void st_async(uint32_t raddr, double v, uint32_t rbar
                ::"r"(raddr), "l"(__double_as_longlong(v)), "r"(rbar) : "memory");
 }
 
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, float a, float b, float c, float d,
+                                            uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+      ::"r"(raddr), "f"(a), "f"(b), "f"(c), "f"(d), "r"(rbar) : "memory");
+}
+
+__device__ __forceinline__ void st_async_v2(uint32_t raddr, double a, double b, uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+      ::"r"(raddr), "d"(a), "d"(b), "r"(rbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -260,6 +293,35 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// TMA: 2D tiled load of box {x, y} (x innermost) into shared memory,
+// completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int32_t x,
+                                            int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+// Bulk (non-tensor) copy global -> shared; size and both addresses must be
+// multiples of 16 bytes.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Host: encode a 2D row-major tensor map (inner = columns) with a box of
+// box_inner x box_outer elements, no swizzle, zero fill out of bounds.
+int make_tmap_2d(CUtensorMap *out, const void *base, int dt, uint64_t inner, uint64_t outer,
+                 uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
+// Same with 128-byte swizzling (tcgen05 K-major operand tiles); box_inner
+// elements must span exactly 128 bytes.
+int make_tmap_2d_sw128(CUtensorMap *out, const void *base, int dt, uint64_t inner,
+                       uint64_t outer, uint64_t row_bytes, uint32_t box_inner,
+                       uint32_t box_outer);
+
 // ---------------------------------------------------------------------------
 // Losses (paper Sec. 2.1): u = dL/dr and L itself
 // ---------------------------------------------------------------------------
@@ -271,7 +333,8 @@ template <> __device__ __forceinline__ float dloss<float>(int loss, float z, flo
     // -y * sigma(-y z) computed without overflow
     const float t = y * z;
     const float e = expf(-fabsf(t));
-    const float sig_neg_t = (t >= 0.f) ? e / (1.f + e) : 1.f / (1.f + e);
+    const float inv = __frcp_rn(1.f + e);
+    const float sig_neg_t = (t >= 0.f) ? e * inv : inv;
     return -y * sig_neg_t;
   }
   return z - y;
@@ -332,8 +395,11 @@ struct Handle {
   unsigned *dflag = nullptr;    // device flag word
   double *loss_partials = nullptr;
   double *loss_out = nullptr;   // device double
-  // run scratch
-  DevBuf ygram, ygemv, ylab, yscale, gbuf;
+  // run scratch, double-buffered by chunk so the x-independent work of chunk
+  // k+1 (side stream) overlaps the chain of chunk k (handle stream)
+  DevBuf ygram[2], ygemv[2], ylab[2], yscale[2], gbuf[2];
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_bulk[2] = {}, ev_chain[2] = {};
   // captured run graph
   cudaGraphExec_t graph = nullptr;
   RunKey graph_key;
@@ -356,6 +422,7 @@ struct GatherArgs {
   void *out1; int dt1; int64_t ld1;            // primary output (gram operand)
   void *out2; int dt2; int64_t ld2;            // optional second output
   float *ylab; float *rscale;                  // labels / row scales (E4M3)
+  int64_t lab_sb, lab_sbp;                     // label of row r at (r/sb)*sbp + r%sb
 };
 int launch_gather(const GatherArgs &a, cudaStream_t st);
 
@@ -365,12 +432,17 @@ struct GramArgs {
   int64_t nouter, rows;   // rows valid in total (tail masking)
   int s; int64_t b, n;
   float *G;
+  unsigned *flag;         // device flag word for FLAG_TIMEOUT, or null
 };
 int launch_gram_simt(const GramArgs &a, cudaStream_t st);
 int launch_gram_tc(const GramArgs &a, cudaStream_t st);
 bool gram_tc_supported(int dt, int64_t ld);
 
+// residual-path division: reciprocal rounded to nearest (one extra rounding)
+__device__ __forceinline__ float fast_rcp(float v) { return __frcp_rn(v); }
+
 struct ChainArgs {
+  CUtensorMap ymap;       // 2D map over the staged GEMV operand rows (TMA)
   const void *Y; int dt; int64_t ldy;
   const float *ylab;
   const float *G;
@@ -380,6 +452,8 @@ struct ChainArgs {
   int s, s_last, nouter, loss;
   float alpha;
   int rec64, kahan, cluster;
+  int64_t sbp;            // labels of outer step h start at ylab[h * sbp]
+  int prefetch;           // 1: stage Y / labels / G through shared memory
   double cpow[257];    // c^j, j = 0..s
   double cinv[257];    // c^-j
 };

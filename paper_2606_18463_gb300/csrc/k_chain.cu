@@ -12,12 +12,19 @@
 //    corrected margins
 //        z_j = c^j r_j - alpha c^{j-1} sum_{i<j} G_{j,i} (c^{-i} u_i)
 //    and residuals, then sends c^{-j} u_j to every CTA.
-// All exchanges are one-way: values travel with st.async into the owner's
-// shared memory and complete transaction bytes on the owner's mbarrier, so
-// an inner step costs one DSMEM latency instead of a cluster barrier.  Every
-// wait is bounded (FLAG_TIMEOUT, then the kernel unwinds without writing x).
-// The own rows of G_{j,<j} stream into shared memory with cp.async one inner
-// step ahead (double buffer) when they fit.
+//
+// Warp roles in each CTA: 16 consumer warps do the arithmetic above and
+// synchronise among themselves only (named barrier 1); one producer warp
+// streams everything x-independent into shared memory ahead of use -- the
+// CTA's column slice of the rows of Y and their labels (TMA 2D tiles and a
+// bulk copy, `ns` outer steps in flight) and the own rows of G_{j,<j} (bulk
+// copies; a whole outer step ahead when two steps fit, else one block row
+// ahead) -- gated by full / empty mbarriers.  x-dependent values travel one
+// way: (vector) st.async into the owner's shared memory, completing
+// transaction bytes on the owner's mbarrier, so an inner step costs one
+// DSMEM latency and no cluster barrier.  Every wait is bounded
+// (FLAG_TIMEOUT; the kernel then drains its own copies and unwinds without
+// writing x).  Slices that do not fit are read from global memory directly.
 //
 // The c^{-i} scaling of the stored residual history turns the per-block
 // weights c^{j-1-i} of the ridge-decayed recurrence into one scalar per row
@@ -31,20 +38,26 @@ namespace cg = cooperative_groups;
 namespace glm {
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
+constexpr int kCThreads = 512;              // consumer threads (warps 0..15)
+constexpr int kCWarps = kCThreads / 32;
+constexpr int kThreads = kCThreads + 32;    // + one producer warp
 constexpr long long kWaitBudget = 4000000000ll;  // SM cycles (~2 s)
-constexpr size_t kSmemMax = 227 * 1024;
+constexpr size_t kSmemMax = 227 * 1024 - 2048;  // leave room for static shared memory
+constexpr int kMaxSlots = 4;
+
+enum { G_NONE = 0, G_STEP = 2, G_BLOCK = 3 };
 
 struct Layout {
-  int nc, rpb, C, gpre;
-  int64_t gbuf_floats;  // one of the two G buffers
-  size_t off_uh, off_rrecv, off_rown, off_yown, off_red, off_part, off_unew, off_bar,
-      off_gbuf, total;
+  int nc, rpb, C, gmode, ns, box_rows, nbox;
+  int64_t gslot_floats;    // floats per G slot (two slots)
+  int64_t ylab_off;        // byte offset of the labels inside a Y slot
+  int64_t yslot;           // bytes per Y slot
+  size_t off_uh, off_rrecv, off_rown, off_yown, off_red, off_part, off_bar, off_coef,
+      off_rem, off_gbuf, off_ybuf, total;
 };
 
 __host__ __device__ inline Layout make_layout(int64_t n, int64_t b, int s, int C,
-                                              int tr_bytes) {
+                                              int tr_bytes, int ev, int want_prefetch) {
   Layout L;
   L.C = C;
   const int64_t per = (n + C - 1) / C;
@@ -54,38 +67,68 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t b, int s, int C
   L.rpb = (int)((b + C - 1) / C);
   const int64_t sb = (int64_t)s * b;
   size_t off = 0;
-  auto take = [&](size_t bytes) {
+  auto take = [&](size_t bytes, size_t align) {
+    off = (off + align - 1) / align * align;
     size_t o = off;
-    off += (bytes + 15) / 16 * 16;
+    off += bytes;
     return o;
   };
-  take((size_t)nc * 4);  // x slice at 0
-  L.off_uh = take((size_t)sb * tr_bytes);
-  L.off_rrecv = take((size_t)C * s * L.rpb * 4);
-  L.off_rown = take((size_t)s * L.rpb * tr_bytes);
-  L.off_yown = take((size_t)s * L.rpb * 4);
-  L.off_red = take((size_t)(L.rpb > kWarps ? L.rpb : kWarps) * tr_bytes);
-  L.off_part = take((size_t)kThreads * 8 * 4);
-  L.off_unew = take((size_t)L.rpb * tr_bytes);
-  L.off_bar = take(4 * 8);
-  L.gbuf_floats = s >= 2 ? (int64_t)L.rpb * gram_ld(s - 1, b) : 0;
-  L.gpre = 0;
-  L.off_gbuf = off;
-  if (s >= 2 && off + 2 * (size_t)L.gbuf_floats * 4 <= kSmemMax) {
-    L.gpre = 1;
-    take(2 * (size_t)L.gbuf_floats * 4);
-  }
-  L.total = off;
+  take((size_t)nc * 4, 16);  // x slice at 0
+  L.off_uh = take((size_t)sb * tr_bytes, 16);
+  L.off_rrecv = take((size_t)C * s * L.rpb * 4, 16);
+  L.off_rown = take((size_t)s * L.rpb * tr_bytes, 16);
+  L.off_yown = take((size_t)s * L.rpb * 4, 16);
+  L.off_red = take((size_t)(L.rpb > kCWarps ? L.rpb : kCWarps) * tr_bytes, 16);
+  L.off_part = take((size_t)kCThreads * 8 * 4, 16);
+  L.off_bar = take(16 * 8, 16);
+  L.off_coef = take((size_t)3 * (s + 1) * tr_bytes, 16);  // c^j, c^-j, alpha c^(j-1)
+  L.off_rem = take((size_t)4 * 16 * 4, 16);                 // mapa'd remote addresses
+  const size_t base = off;
+  // G staging: whole outer step (own rows of every block row) or one block row
+  const int64_t g_step = s >= 2 ? (int64_t)L.rpb * gram_size(s, b) / b : 0;
+  const int64_t g_blk = s >= 2 ? (int64_t)L.rpb * gram_ld(s - 1, b) : 0;
+  L.box_rows = sb >= 256 ? 256 : (int)round_up(sb, 8);
+  L.nbox = (int)((sb + L.box_rows - 1) / L.box_rows);
+  L.ylab_off = round_up((int64_t)L.nbox * L.box_rows * nc * ev, 128);
+  L.yslot = round_up(L.ylab_off + round_up(sb, 4) * 4, 1024);
+  const int ystage = want_prefetch && nc <= 256;  // TMA box limit
+  L.gmode = G_NONE;
+  L.ns = 0;
+  L.gslot_floats = 0;
+  auto fits = [&](int64_t gfl, int ns) {
+    const size_t g_end = round_up(base, 16) + 2 * (size_t)gfl * 4;
+    return round_up(g_end, 1024) + (size_t)ns * L.yslot + (ns ? 1024 : 0) <= kSmemMax;
+  };
+  const int gm[3] = {G_STEP, G_BLOCK, G_NONE};
+  const int64_t gf[3] = {g_step, g_blk, 0};
+  bool done = false;
+  for (int ns = kMaxSlots; ns >= 2 && ystage && !done; --ns)
+    for (int q = 0; q < 3 && !done; ++q)
+      if ((q == 2 || s >= 2) && fits(gf[q], ns)) {
+        L.ns = ns; L.gmode = gm[q]; L.gslot_floats = gf[q]; done = true;
+      }
+  for (int q = 0; q < 2 && !done && want_prefetch && s >= 2; ++q)
+    if (fits(gf[q], 0)) { L.gmode = gm[q]; L.gslot_floats = gf[q]; done = true; }
+  off = base;
+  L.off_gbuf = take(2 * (size_t)L.gslot_floats * 4, 16);
+  L.off_ybuf = take(L.ns ? (size_t)L.ns * L.yslot : 0, 1024);
+  L.total = off + (L.ns ? 1024 : 0);  // slack to 1024-align the Y slots at run time
   return L;
 }
 
-// Raw 8-element vector loads kept in registers until converted.
+// Raw 8-element vector loads kept in registers until converted.  `shared`
+// selects a plain (shared-memory) load instead of the read-only global path.
 template <typename T> struct Raw8;
 template <> struct Raw8<float> {
   float4 a, b;
-  __device__ __forceinline__ void load(const float *p) {
-    a = __ldg(reinterpret_cast<const float4 *>(p));
-    b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+  __device__ __forceinline__ void load(const float *p, bool shared) {
+    if (shared) {
+      a = reinterpret_cast<const float4 *>(p)[0];
+      b = reinterpret_cast<const float4 *>(p)[1];
+    } else {
+      a = __ldg(reinterpret_cast<const float4 *>(p));
+      b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    }
   }
   __device__ __forceinline__ void zero() { a = b = make_float4(0.f, 0.f, 0.f, 0.f); }
   __device__ __forceinline__ void get(float (&o)[8]) const {
@@ -95,8 +138,8 @@ template <> struct Raw8<float> {
 };
 template <> struct Raw8<__nv_bfloat16> {
   uint4 w;
-  __device__ __forceinline__ void load(const __nv_bfloat16 *p) {
-    w = __ldg(reinterpret_cast<const uint4 *>(p));
+  __device__ __forceinline__ void load(const __nv_bfloat16 *p, bool shared) {
+    w = shared ? *reinterpret_cast<const uint4 *>(p) : __ldg(reinterpret_cast<const uint4 *>(p));
   }
   __device__ __forceinline__ void zero() { w = make_uint4(0, 0, 0, 0); }
   __device__ __forceinline__ void get(float (&o)[8]) const {
@@ -110,8 +153,8 @@ template <> struct Raw8<__nv_bfloat16> {
 };
 template <> struct Raw8<__half> {
   uint4 w;
-  __device__ __forceinline__ void load(const __half *p) {
-    w = __ldg(reinterpret_cast<const uint4 *>(p));
+  __device__ __forceinline__ void load(const __half *p, bool shared) {
+    w = shared ? *reinterpret_cast<const uint4 *>(p) : __ldg(reinterpret_cast<const uint4 *>(p));
   }
   __device__ __forceinline__ void zero() { w = make_uint4(0, 0, 0, 0); }
   __device__ __forceinline__ void get(float (&o)[8]) const {
@@ -125,11 +168,13 @@ template <> struct Raw8<__half> {
   }
 };
 
-constexpr int kUnroll = 4;
+constexpr int kRows = 4;  // consecutive rows per thread group in the margin
+
+__device__ __forceinline__ void csync() { named_sync(1, kCThreads); }
 
 template <typename TY, typename TR>
 __global__ void __launch_bounds__(kThreads, 1)
-k_chain(const ChainArgs a) {
+k_chain(const __grid_constant__ ChainArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -137,13 +182,13 @@ k_chain(const ChainArgs a) {
   const int64_t n = a.n, b = a.b;
   const int s = a.s;
   const int64_t sb = (int64_t)s * b;
-  const Layout L = make_layout(n, b, s, C, (int)sizeof(TR));
-  const int nc = L.nc, rpb = L.rpb;
+  const Layout L = make_layout(n, b, s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
+  const int nc = L.nc, rpb = L.rpb, ns = L.ns, gmode = L.gmode;
   const int64_t col0 = (int64_t)rank * nc;
   const int64_t l0 = (int64_t)rank * rpb;
   const int nown = (int)max((int64_t)0, min((int64_t)rpb, b - l0));
 
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   float *xs = reinterpret_cast<float *>(smem);
   TR *uh = reinterpret_cast<TR *>(smem + L.off_uh);
   float *rrecv = reinterpret_cast<float *>(smem + L.off_rrecv);
@@ -152,119 +197,276 @@ k_chain(const ChainArgs a) {
   TR *red = reinterpret_cast<TR *>(smem + L.off_red);
   float *part = reinterpret_cast<float *>(smem + L.off_part);
   float *gbuf = reinterpret_cast<float *>(smem + L.off_gbuf);
+  const uint32_t sbase = smem_u32(smem);
+  unsigned char *ybuf = smem + (round_up(sbase + L.off_ybuf, 1024) - sbase);
+  TR *cpw = reinterpret_cast<TR *>(smem + L.off_coef);   // c^j
+  TR *cinw = cpw + (s + 1);                                // c^-j
+  TR *zcw = cinw + (s + 1);                                // alpha c^(j-1), j >= 1
+  uint32_t *rem = reinterpret_cast<uint32_t *>(smem + L.off_rem);
   __shared__ int s_abort;
-  const uint32_t bar_r = smem_u32(smem + L.off_bar);
-  const uint32_t bar_u[2] = {bar_r + 8, bar_r + 16};
+
+  const uint32_t bar0 = smem_u32(smem + L.off_bar);
+  const uint32_t bar_r = bar0;                       // margin partials
+  const uint32_t bar_u0 = bar0 + 8;                  // residuals (x2)
+  const uint32_t full_g0 = bar0 + 24, empty_g0 = bar0 + 40;   // x2 each
+  const uint32_t full_y0 = bar0 + 56, empty_y0 = bar0 + 88;   // x kMaxSlots each
 
   if (tid == 0) {
-    mbar_init(bar_r, 1);
-    mbar_init(bar_u[0], 1);
-    mbar_init(bar_u[1], 1);
+    for (int i = 0; i < 15; ++i) mbar_init(bar0 + 8 * i, 1);
     fence_mbar_init_cluster();
     s_abort = 0;
   }
-  const TY *Y = static_cast<const TY *>(a.Y);
+  for (int j = tid; j <= s; j += kThreads) {
+    cpw[j] = (TR)a.cpow[j];
+    cinw[j] = (TR)a.cinv[j];
+    zcw[j] = j > 0 ? (TR)((double)a.alpha * a.cpow[j - 1]) : (TR)0;
+  }
+  if (tid < C) {  // remote views of the exchange buffers and their barriers
+    rem[tid] = mapa(smem_u32(rrecv), tid);
+    rem[16 + tid] = mapa(bar_r, tid);
+    rem[32 + tid] = mapa(smem_u32(uh), tid);
+    rem[48 + tid] = mapa(bar_u0, tid);
+  }
   for (int c = tid; c < nc; c += kThreads) xs[c] = (col0 + c < n) ? a.x[col0 + c] : 0.f;
   const int64_t gsz = gram_size(s, b);
   // barriers initialised in every CTA before any remote traffic
   cluster.sync();
 
+  // ========================= producer warp ===================================
+  if (warp == kCWarps) {
+    if (lane == 0) {
+      const uint32_t ystep_bytes =
+          (uint32_t)((int64_t)L.nbox * L.box_rows * nc * sizeof(TY) + round_up(sb, 4) * 4);
+      int64_t kblk = 0;          // G block rows issued so far (G_BLOCK mode)
+      int y_iss = 0, g_iss = 0;  // copies issued (for the abort drain)
+      volatile int *vabort = &s_abort;
+      for (int hh = 0; hh < a.nouter && !*vabort; ++hh) {
+        const int shh = (hh == a.nouter - 1) ? a.s_last : s;
+        if (ns) {
+          const int slot = hh % ns;
+          if (hh >= ns && !mbar_wait_bounded(empty_y0 + 8 * slot,
+                                             (uint32_t)((hh / ns - 1) & 1), kWaitBudget)) {
+            atomicOr(&s_abort, 1);
+            break;
+          }
+          const uint32_t bar = full_y0 + 8 * slot;
+          const uint32_t dst = smem_u32(ybuf + (int64_t)slot * L.yslot);
+          mbar_arrive_expect_tx(bar, ystep_bytes);
+          for (int k = 0; k < L.nbox; ++k)
+            tma_load_2d(dst + (uint32_t)((int64_t)k * L.box_rows * nc * sizeof(TY)), &a.ymap,
+                        (int32_t)col0, (int32_t)((int64_t)hh * sb + (int64_t)k * L.box_rows),
+                        bar);
+          bulk_load(dst + (uint32_t)L.ylab_off, a.ylab + (int64_t)hh * a.sbp,
+                    (uint32_t)(round_up(sb, 4) * 4), bar);
+          ++y_iss;
+        }
+        if (gmode == G_STEP && shh >= 2) {
+          const int slot = hh & 1;
+          if (hh >= 2 && !mbar_wait_bounded(empty_g0 + 8 * slot,
+                                            (uint32_t)(((hh >> 1) - 1) & 1), kWaitBudget)) {
+            atomicOr(&s_abort, 1);
+            break;
+          }
+          const uint32_t bar = full_g0 + 8 * slot;
+          const float *Gh = a.G + (int64_t)hh * gsz;
+          const uint32_t dst = smem_u32(gbuf + slot * L.gslot_floats);
+          int64_t bytes = 0;
+          for (int j = 1; j < shh; ++j) bytes += (int64_t)nown * gram_ld(j, b) * 4;
+          mbar_arrive_expect_tx(bar, (uint32_t)bytes);
+          int64_t soff = 0;  // floats into the slot
+          for (int j = 1; j < shh; ++j) {
+            const int64_t ldj = gram_ld(j, b);
+            bulk_load(dst + (uint32_t)(soff * 4), Gh + gram_off(j, b) + l0 * ldj,
+                      (uint32_t)(nown * ldj * 4), bar);
+            soff += (int64_t)rpb * ldj;
+          }
+          ++g_iss;
+        } else if (gmode == G_BLOCK) {
+          const float *Gh = a.G + (int64_t)hh * gsz;
+          bool stop = false;
+          for (int j = 1; j < shh; ++j, ++kblk) {
+            const int slot = (int)(kblk & 1);
+            if (kblk >= 2 && !mbar_wait_bounded(empty_g0 + 8 * slot,
+                                                (uint32_t)(((kblk >> 1) - 1) & 1), kWaitBudget)) {
+              atomicOr(&s_abort, 1);
+              stop = true;
+              break;
+            }
+            const int64_t ldj = gram_ld(j, b);
+            const uint32_t bar = full_g0 + 8 * slot;
+            mbar_arrive_expect_tx(bar, (uint32_t)(nown * ldj * 4));
+            bulk_load(smem_u32(gbuf + slot * L.gslot_floats), Gh + gram_off(j, b) + l0 * ldj,
+                      (uint32_t)(nown * ldj * 4), bar);
+            ++g_iss;
+          }
+          if (stop) break;
+        }
+      }
+      if (*vabort) {
+        // wait (bounded) until every copy this warp issued has landed: the
+        // i-th fill of a two-phase slot completes phase i, so the last fill
+        // of each slot is awaited with the parity of its own phase
+        for (int k = 0; k < ns && k < y_iss; ++k) {
+          const int last = ((y_iss - 1 - k) / ns) * ns + k;  // last fill of slot k
+          mbar_wait_bounded(full_y0 + 8 * k, (uint32_t)((last / ns) & 1), kWaitBudget);
+        }
+        for (int k = 0; k < 2 && k < g_iss; ++k) {
+          const int last = ((g_iss - 1 - k) / 2) * 2 + k;
+          mbar_wait_bounded(full_g0 + 8 * k, (uint32_t)((last / 2) & 1), kWaitBudget);
+        }
+      }
+    }
+    __syncwarp();
+    cluster.sync();
+    return;
+  }
+
+  // ========================= consumer warps ==================================
   const int V = nc / 8;               // 8-element vectors in the slice
   const int tpr = V < 32 ? V : 32;    // threads per row in the margin
   const int vpt = V / tpr;            // vectors per thread per row
-  const int rpp = kThreads / tpr;     // rows per pass
+  const int groups = kCThreads / tpr; // row groups (kRows consecutive rows each)
   const int gi = tid / tpr, li = tid % tpr;
-  const uint32_t rrecv_a = smem_u32(rrecv), uh_a = smem_u32(uh);
-  uint32_t J = 0;  // inner steps completed in this launch
+  const bool vsend_r = (b % 4 == 0) && (rpb % 4 == 0);            // 4 rows -> one v4
+  const bool vsend_u = sizeof(TR) == 4 ? (b % 4 == 0 && rpb % 4 == 0)
+                                       : (b % 2 == 0 && rpb % 2 == 0);
+  const int upk = sizeof(TR) == 4 ? 4 : 2;                        // values per vector send
+  const int loss_kind = a.loss;
+  unsigned *const flag = a.flag;
+  const TY *Y = static_cast<const TY *>(a.Y);
+  uint32_t J = 0;         // inner steps completed in this launch
+  int64_t kblk = 0;       // G block rows consumed (G_BLOCK mode)
   bool abort = false;
 
   for (int h = 0; h < a.nouter && !abort; ++h) {
     const int sh = (h == a.nouter - 1) ? a.s_last : s;
     const int64_t R = (int64_t)sh * b;
     const int64_t row0 = (int64_t)h * sb;
-    const TY *Yh = Y + row0 * a.ldy;
     const float *Gh = a.G + (int64_t)h * gsz;
     if (tid == 0) mbar_arrive_expect_tx(bar_r, (uint32_t)(C * sh * nown * 4));
-
-    // G rows of block j (own rows) -> gbuf[j & 1], 16-byte async copies
-    auto g_prefetch = [&](int j) {
-      const int64_t ldj = gram_ld(j, b);
-      const float *src = Gh + gram_off(j, b) + l0 * ldj;
-      float *dst = gbuf + (j & 1) * L.gbuf_floats;
-      const int64_t chunks = (int64_t)nown * ldj / 4;
-      for (int64_t q = tid; q < chunks; q += kThreads) cp_async16(smem_u32(dst + 4 * q), src + 4 * q);
-    };
-    if (L.gpre && sh >= 2) g_prefetch(1);
-    cp_async_commit();
+    const bool staged = ns > 0;
+    const TY *Ys;          // row r of this CTA's slice at Ys + r * ystride
+    int64_t ystride;
+    const float *labs;
+    if (staged) {
+      const int slot = h % ns;
+      if (!mbar_wait_bounded(full_y0 + 8 * slot, (uint32_t)((h / ns) & 1), kWaitBudget))
+        atomicOr(&s_abort, 1);
+      Ys = reinterpret_cast<const TY *>(ybuf + (int64_t)slot * L.yslot);
+      ystride = nc;
+      labs = reinterpret_cast<const float *>(ybuf + (int64_t)slot * L.yslot + L.ylab_off);
+    } else {
+      Ys = Y + row0 * a.ldy + col0;
+      ystride = a.ldy;
+      labs = a.ylab + (int64_t)h * a.sbp;
+    }
 
     // ---- A: partial margins over this CTA's column slice --------------------
-    for (int64_t rb = 0; rb < R; rb += (int64_t)rpp * kUnroll) {
-      float acc[kUnroll];
+    for (int64_t rb = 0; rb < R; rb += (int64_t)groups * kRows) {
+      const int64_t r0 = rb + (int64_t)gi * kRows;   // this group's first row
+      float acc[kRows];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) acc[u] = 0.f;
+      for (int u = 0; u < kRows; ++u) acc[u] = 0.f;
       for (int v0 = 0; v0 < vpt; ++v0) {
         const int64_t col = (int64_t)(li + v0 * tpr) * 8;
         const bool colok = col0 + col < n;
-        Raw8<TY> raw[kUnroll];
+        float xv[8];
+        {
+          const float4 x0 = reinterpret_cast<const float4 *>(xs + col)[0];
+          const float4 x1 = reinterpret_cast<const float4 *>(xs + col)[1];
+          xv[0] = x0.x; xv[1] = x0.y; xv[2] = x0.z; xv[3] = x0.w;
+          xv[4] = x1.x; xv[5] = x1.y; xv[6] = x1.z; xv[7] = x1.w;
+        }
+        Raw8<TY> raw[kRows];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int64_t r = rb + gi + (int64_t)u * rpp;
-          if (r < R && colok) raw[u].load(Yh + r * a.ldy + col0 + col);
+        for (int u = 0; u < kRows; ++u) {
+          if (r0 + u < R && colok) raw[u].load(Ys + (r0 + u) * ystride + col, staged);
           else raw[u].zero();
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kRows; ++u) {
           float f[8];
           raw[u].get(f);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc[u] = fmaf(f[i], xs[col + i], acc[u]);
+          for (int i = 0; i < 8; ++i) acc[u] = fmaf(f[i], xv[i], acc[u]);
         }
       }
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < kRows; ++u)
         for (int off = tpr / 2; off > 0; off >>= 1)
           acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], off);
-        const int64_t r = rb + gi + (int64_t)u * rpp;
-        if (li == 0 && r < R) {
-          const int64_t j = r / b, l = r - j * b;
-          const int owner = (int)(l / rpb);
-          const int64_t ll = l - (int64_t)owner * rpb;
-          const uint32_t dst = rrecv_a + (uint32_t)((((int64_t)rank * s + j) * rpb + ll) * 4);
-          st_async(mapa(dst, owner), acc[u], mapa(bar_r, owner));
+      if (li == 0 && r0 < R) {
+        const int64_t j = r0 / b, l = r0 - j * b;
+        const int owner = (int)(l / rpb);
+        const int64_t ll = l - (int64_t)owner * rpb;
+        const uint32_t off4 = (uint32_t)((((int64_t)rank * s + j) * rpb + ll) * 4);
+        if (vsend_r) {  // the 4 rows share block, owner and a 16-byte slot
+          st_async_v4(rem[owner] + off4, acc[0], acc[1], acc[2], acc[3], rem[16 + owner]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < kRows; ++u) {
+            const int64_t r = r0 + u;
+            if (r < R) {
+              const int64_t ju = r / b, lu = r - ju * b;
+              const int ow = (int)(lu / rpb);
+              const int64_t lw = lu - (int64_t)ow * rpb;
+              st_async(rem[ow] + (uint32_t)((((int64_t)rank * s + ju) * rpb + lw) * 4), acc[u],
+                       rem[16 + ow]);
+            }
+          }
         }
       }
     }
     if (!mbar_wait_bounded(bar_r, h & 1, kWaitBudget)) atomicOr(&s_abort, 1);
-    __syncthreads();
+    csync();
     if (s_abort) { abort = true; break; }
 
-    // ---- C: own rows' margins (fixed summation order) and labels -----------
-    for (int t = tid; t < sh * nown; t += kThreads) {
-      const int j = t / nown, ll = t - j * nown;
-      TR sum = 0;
-      for (int src = 0; src < C; ++src) sum += (TR)rrecv[((int64_t)src * s + j) * rpb + ll];
-      rown[j * rpb + ll] = sum;
-      yown[j * rpb + ll] = a.ylab[row0 + (int64_t)j * b + l0 + ll];
+    // ---- C: own rows' margins (C-way shuffle trees, fixed order) and labels --
+    {
+      const int per = kCThreads / C;
+      const int e_local = tid / C, src = tid - (tid / C) * C;
+      for (int e0 = 0; e0 < sh * nown; e0 += per) {
+        const int e = e0 + e_local;
+        TR v = 0;
+        if (e < sh * nown) {
+          const int j = e / nown, ll = e - j * nown;
+          v = (TR)rrecv[((int64_t)src * s + j) * rpb + ll];
+        }
+        for (int off = C / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (src == 0 && e < sh * nown) {
+          const int j = e / nown, ll = e - j * nown;
+          rown[j * rpb + ll] = v;
+          yown[j * rpb + ll] = labs[(int64_t)j * b + l0 + ll];
+        }
+      }
     }
-    __syncthreads();
+    if (gmode == G_STEP && sh >= 2) {
+      if (!mbar_wait_bounded(full_g0 + 8 * (h & 1), (uint32_t)((h >> 1) & 1), kWaitBudget))
+        atomicOr(&s_abort, 1);
+    }
+    csync();
+    if (s_abort) { abort = true; break; }
 
     // ---- D: inner s-step recurrence -----------------------------------------
-    const int wpr = nown > 0 ? max(1, kWarps / nown) : 1;
+    const int wpr = nown > 0 ? max(1, kCWarps / nown) : 1;
+    int64_t goff = 0;   // floats into the G_STEP slot
     for (int j = 0; j < sh; ++j) {
       if (j > 0) {
         const int64_t jb = (int64_t)j * b;
         const int64_t ldj = gram_ld(j, b);
         const float *gsrc;
-        if (L.gpre) {
-          if (j + 1 < sh) g_prefetch(j + 1);
-          cp_async_commit();
-          cp_async_wait<1>();
-          __syncthreads();
-          gsrc = gbuf + (j & 1) * L.gbuf_floats;
+        if (gmode == G_STEP) {
+          gsrc = gbuf + (h & 1) * L.gslot_floats + goff;
+          goff += (int64_t)rpb * ldj;
+        } else if (gmode == G_BLOCK) {
+          if (!mbar_wait_bounded(full_g0 + 8 * (kblk & 1), (uint32_t)((kblk >> 1) & 1),
+                                 kWaitBudget))
+            atomicOr(&s_abort, 1);
+          gsrc = gbuf + (kblk & 1) * L.gslot_floats;
         } else {
           gsrc = Gh + gram_off(j, b) + l0 * ldj;
         }
-        for (int item = warp; item < nown * wpr; item += kWarps) {
+        for (int item = warp; item < nown * wpr; item += kCWarps) {
           const int rr = item / wpr, pp = item - rr * wpr;
           const float *grow = gsrc + rr * ldj;
           TR acc0 = 0, acc1 = 0;
@@ -280,48 +482,95 @@ k_chain(const ChainArgs a) {
           for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
           if (lane == 0) red[item] = acc;
         }
-        __syncthreads();
+        csync();
+        if (gmode == G_BLOCK) {
+          if (tid == 0) mbar_arrive(empty_g0 + 8 * (kblk & 1));
+          ++kblk;
+        }
       }
-      if (tid < nown) {
-        TR corr = 0;
-        if (j > 0)
-          for (int p = 0; p < wpr; ++p) corr += red[tid * wpr + p];
-        const TR rj = rown[j * rpb + tid];
-        const TR z = (TR)a.cpow[j] * rj -
-                     (j > 0 ? (TR)a.alpha * (TR)a.cpow[j - 1] * corr : (TR)0);
-        const TR u = dloss<TR>(a.loss, z, (TR)yown[j * rpb + tid]);
-        if (!isfinite(z) || !isfinite(u)) atomicOr(a.flag, FLAG_NONFINITE);
-        const TR uw = u * (TR)a.cinv[j];
-        const uint32_t dst = uh_a + (uint32_t)(((int64_t)j * b + l0 + tid) * sizeof(TR));
-        for (int d = 0; d < C; ++d) st_async(mapa(dst, d), uw, mapa(bar_u[J & 1], d));
+      if (warp == 0) {
+        // residuals of the own rows (lanes < nown), then warp 0 fans the
+        // sends out across its lanes (16-byte vectors when aligned)
+        for (int rb0 = 0; rb0 < nown; rb0 += 32) {
+          const int rr = rb0 + lane;
+          TR uw = 0;
+          if (rr < nown) {
+            TR corr = 0;
+            if (j > 0)
+              for (int p = 0; p < wpr; ++p) corr += red[rr * wpr + p];
+            const TR z = cpw[j] * rown[j * rpb + rr] - zcw[j] * corr;
+            const TR u = dloss<TR>(loss_kind, z, (TR)yown[j * rpb + rr]);
+            if (!isfinite(z) || !isfinite(u)) atomicOr(flag, FLAG_NONFINITE);
+            uw = u * cinw[j];
+          }
+          const int nrow = min(32, nown - rb0);
+          const uint32_t ubase = (uint32_t)(((int64_t)j * b + l0 + rb0) * sizeof(TR));
+          const uint32_t ubar = 8 * (J & 1);
+          if (vsend_u) {
+            const int cnt = (nrow / upk) * C;
+            for (int t0 = 0; t0 < cnt; t0 += 32) {
+              const int t = t0 + lane;
+              const int chunk = (t < cnt) ? t / C : 0;
+              const int d = t - chunk * C;
+              if (sizeof(TR) == 4) {
+                const float v0 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk);
+                const float v1 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk + 1);
+                const float v2 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk + 2);
+                const float v3 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk + 3);
+                if (t < cnt)
+                  st_async_v4(rem[32 + d] + ubase + 16 * chunk, v0, v1, v2, v3,
+                              rem[48 + d] + ubar);
+              } else {
+                const double v0 = __shfl_sync(0xffffffffu, (double)uw, 2 * chunk);
+                const double v1 = __shfl_sync(0xffffffffu, (double)uw, 2 * chunk + 1);
+                if (t < cnt)
+                  st_async_v2(rem[32 + d] + ubase + 16 * chunk, v0, v1, rem[48 + d] + ubar);
+              }
+            }
+          } else {
+            const int cnt = nrow * C;
+            for (int t0 = 0; t0 < cnt; t0 += 32) {
+              const int t = t0 + lane;
+              const int src_lane = (t < cnt) ? t / C : 0;
+              const TR v = __shfl_sync(0xffffffffu, uw, src_lane);
+              if (t < cnt) {
+                const int d = t - src_lane * C;
+                st_async(rem[32 + d] + ubase + (uint32_t)(src_lane * sizeof(TR)), v,
+                         rem[48 + d] + ubar);
+              }
+            }
+          }
+        }
       }
-      if (tid == 0) mbar_arrive_expect_tx(bar_u[J & 1], (uint32_t)(b * sizeof(TR)));
-      if (!mbar_wait_bounded(bar_u[J & 1], (J >> 1) & 1, kWaitBudget)) atomicOr(&s_abort, 1);
+      if (tid == 0) mbar_arrive_expect_tx(bar_u0 + 8 * (J & 1), (uint32_t)(b * sizeof(TR)));
+      if (!mbar_wait_bounded(bar_u0 + 8 * (J & 1), (J >> 1) & 1, kWaitBudget))
+        atomicOr(&s_abort, 1);
       ++J;
-      __syncthreads();
+      csync();
       if (s_abort) { abort = true; break; }
     }
     if (abort) break;
+    if (gmode == G_STEP && sh >= 2 && tid == 0) mbar_arrive(empty_g0 + 8 * (h & 1));
 
     // ---- E: x <- c^{sh} x - alpha c^{sh-1} Y^T (c^{-j} u), own slice ---------
     {
-      const int RG = kThreads / V;
+      const int RG = kCThreads / V;
       const int g = tid / V, v = tid - (tid / V) * V;
       const int64_t col = (int64_t)v * 8;
       float acc[8], cmp[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) { acc[i] = 0.f; cmp[i] = 0.f; }
       if (g < RG && col0 + col < n) {
-        for (int64_t rb = g; rb < R; rb += (int64_t)RG * kUnroll) {
-          Raw8<TY> raw[kUnroll];
+        for (int64_t rb = g; rb < R; rb += (int64_t)RG * 4) {
+          Raw8<TY> raw[4];
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
+          for (int u = 0; u < 4; ++u) {
             const int64_t r = rb + (int64_t)u * RG;
-            if (r < R) raw[u].load(Yh + r * a.ldy + col0 + col);
+            if (r < R) raw[u].load(Ys + r * ystride + col, staged);
             else raw[u].zero();
           }
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
+          for (int u = 0; u < 4; ++u) {
             const int64_t r = rb + (int64_t)u * RG;
             if (r >= R) break;
             float f[8];
@@ -346,31 +595,50 @@ k_chain(const ChainArgs a) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) part[(int64_t)g * nc + col + i] = acc[i];
       }
-      __syncthreads();
-      const float decay = (float)a.cpow[sh];
-      const float stp = (float)((double)a.alpha * a.cpow[sh - 1]);
-      for (int c = tid; c < nc; c += kThreads) {
+      csync();
+      if (staged && tid == 0) mbar_arrive(empty_y0 + 8 * (h % ns));  // Y slot free again
+      const float decay = (float)cpw[sh];
+      const float stp = (float)zcw[sh];
+      // TPC threads per column (consecutive lanes), each Kahan-summing RG/TPC
+      // row-group partials, then a shuffle tree across the TPC lanes
+      const int TPC = nc >= kCThreads ? 1 : kCThreads / nc;
+      for (int c0 = 0; c0 < nc; c0 += kCThreads / TPC) {
+        const int c = c0 + tid / TPC, q = tid % TPC;
         float S = 0.f, cS = 0.f;
-        for (int gg = 0; gg < RG; ++gg) {
-          const float yv = part[(int64_t)gg * nc + c] - cS;
-          const float t2 = S + yv;
-          cS = (t2 - S) - yv;
-          S = t2;
+        if (c < nc) {
+          for (int gg = q; gg < RG; gg += TPC) {
+            const float yv = part[(int64_t)gg * nc + c] - cS;
+            const float t2 = S + yv;
+            cS = (t2 - S) - yv;
+            S = t2;
+          }
         }
-        if (col0 + c < n) {
+        S -= cS;
+        for (int off = (TPC < 32 ? TPC : 32) / 2; off > 0; off >>= 1)
+          S += __shfl_xor_sync(0xffffffffu, S, off);
+        if (TPC > 32) {  // more than a warp per column (only nc = 8)
+          __shared__ float wred[kCWarps];
+          if (lane == 0) wred[warp] = S;
+          csync();
+          if (q == 0 && c < nc) {
+            S = 0.f;
+            for (int w = 0; w < TPC / 32; ++w) S += wred[(tid / 32) + w];
+          }
+          csync();
+        }
+        if (q == 0 && c < nc && col0 + c < n) {
           const float xn = fmaf(-stp, S, decay * xs[c]);
-          if (!isfinite(xn)) atomicOr(a.flag, FLAG_NONFINITE);
+          if (!isfinite(xn)) atomicOr(flag, FLAG_NONFINITE);
           xs[c] = xn;
         }
       }
-      __syncthreads();
+      csync();
     }
   }
-  cp_async_wait<0>();
   if (abort) {
     if (tid == 0) atomicOr(a.flag, FLAG_TIMEOUT);
   } else {
-    for (int c = tid; c < nc; c += kThreads)
+    for (int c = tid; c < nc; c += kCThreads)
       if (col0 + c < n) a.x[col0 + c] = xs[c];
   }
   cluster.sync();
@@ -391,13 +659,27 @@ cudaLaunchConfig_t make_cfg(int C, size_t smem, cudaStream_t st, cudaLaunchAttri
   return cfg;
 }
 
+// every CTA must own at least one row of each block (one-way exchanges rely
+// on each CTA taking part in every inner step)
+bool cluster_rows_ok(int C, int64_t b) {
+  if (C < 1 || (C & (C - 1))) return false;  // shuffle trees need a power of two
+  const int64_t rpb = (b + C - 1) / C;
+  return (int64_t)(C - 1) * rpb < b;
+}
+
 template <typename TY, typename TR>
-int launch_t(const ChainArgs &a, cudaStream_t st) {
+int launch_t(const ChainArgs &a0, cudaStream_t st) {
+  ChainArgs a = a0;
   const int C = a.cluster;
-  const Layout L = make_layout(a.n, a.b, a.s, C, (int)sizeof(TR));
+  const Layout L = make_layout(a.n, a.b, a.s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
   if (L.total > kSmemMax)
     return set_error(GLM_EUNSUPPORTED, "chain: shared-memory need exceeds 227 KB "
                                        "(reduce s*b or raise the cluster size)");
+  if (L.ns) {
+    GLM_TRY(make_tmap_2d(&a.ymap, a.Y, a.dt, (uint64_t)a.ldy,
+                         (uint64_t)a.nouter * a.s * a.b, (uint64_t)a.ldy * sizeof(TY),
+                         (uint32_t)L.nc, (uint32_t)L.box_rows));
+  }
   auto kern = k_chain<TY, TR>;
   GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)L.total));
@@ -409,19 +691,12 @@ int launch_t(const ChainArgs &a, cudaStream_t st) {
   return GLM_OK;
 }
 
-// every CTA must own at least one row of each block (one-way exchanges rely
-// on each CTA taking part in every inner step)
-bool cluster_rows_ok(int C, int64_t b) {
-  const int64_t rpb = (b + C - 1) / C;
-  return (int64_t)(C - 1) * rpb < b;
-}
-
 template <typename TY, typename TR>
 int max_cluster_t(const ChainArgs &a) {
   auto kern = k_chain<TY, TR>;
   for (int C = 16; C >= 1; C /= 2) {
     if (!cluster_rows_ok(C, a.b)) continue;
-    const Layout L = make_layout(a.n, a.b, a.s, C, (int)sizeof(TR));
+    const Layout L = make_layout(a.n, a.b, a.s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
     if (L.total > kSmemMax) continue;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L.total) != cudaSuccess) { cudaGetLastError(); continue; }
@@ -459,7 +734,8 @@ int chain_max_cluster(const ChainArgs &a) {
 int launch_chain(const ChainArgs &a, cudaStream_t st) {
   if (a.nouter <= 0) return GLM_OK;
   if (a.cluster < 1 || a.cluster > 16 || !cluster_rows_ok(a.cluster, a.b))
-    return set_error(GLM_EINVAL, "chain: cluster size must be 1..16 and leave every CTA a row");
+    return set_error(GLM_EINVAL, "chain: cluster size must be a power of two in 1..16 that "
+                                 "leaves every CTA a row of each block");
   const bool f64 = a.rec64 != 0;
   switch (a.dt) {
   case GLM_F32: case GLM_TF32:

@@ -43,7 +43,7 @@ k_gather(GatherArgs a) {
       if (c < a.ld1) store8(d1 + c * elem_bytes(a.dt1), a.dt1, v);
       if (d2 && c < a.ld2) store8(d2 + c * elem_bytes(a.dt2), a.dt2, v);
     }
-    if (lane == 0) a.ylab[row] = __ldg(a.y + idx);
+    if (lane == 0) a.ylab[(row / a.lab_sb) * a.lab_sbp + row % a.lab_sb] = __ldg(a.y + idx);
   }
 }
 
@@ -87,7 +87,7 @@ k_gather_e4m3(GatherArgs a) {
       }
     }
     if (lane == 0) {
-      a.ylab[row] = __ldg(a.y + idx);
+      a.ylab[(row / a.lab_sb) * a.lab_sbp + row % a.lab_sb] = __ldg(a.y + idx);
       a.rscale[row] = __ldg(a.rs8 + idx);
     }
   }

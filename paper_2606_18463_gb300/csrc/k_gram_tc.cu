@@ -1,18 +1,368 @@
-// k_gram_tc.cu -- tcgen05 tensor-core Gram (filled in below).
+// k_gram_tc.cu -- strictly block-lower Gram G_{j,i} = Y_j Y_i^T (i < j) on
+// the 5th-generation tensor cores (paper Algorithm 1, Gram step; Sec. 5.2's
+// G_L is the only part the recurrence reads).
+//
+// One persistent CTA per SM walks a static list of 128 x 128 output tiles of
+// the lower triangle of every outer iteration's (s b) x (s b) Gram; tiles
+// holding no strictly-lower block entry are skipped.  Warp roles:
+//   warp 0      TMA producer: both operand tiles (rows of Y, K-major, 128-byte
+//               swizzle) per 128-byte K chunk into a STAGES-deep ring;
+//   warp 1      allocates 256 TMEM columns (two 128-column FP32 accumulators)
+//               and one elected lane issues tcgen05.mma (M=128, N=128), four
+//               MMAs per K chunk, committing each stage back to the producer
+//               and each finished accumulator to the epilogue;
+//   warps 2..5  epilogue: tcgen05.ld 32x32b rows out of TMEM, per-row scales
+//               (E4M3), masked FP32 stores into the padded row-block layout.
+// Operand kinds: BF16 / F16 (kind::f16), TF32 (kind::tf32, FP32 container
+// already rounded to TF32), E4M3 (kind::f8f6f4, one power-of-two scale per row
+// applied at readout).  Accumulation is FP32 throughout.  Every mbarrier wait
+// is bounded; on timeout the kernel records FLAG_TIMEOUT, drains its own
+// work (bounded) and frees its TMEM.
 #include "glm_internal.cuh"
 
 namespace glm {
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kTile = 128;                 // M = N = 128
+constexpr int kChunkBytes = 128;           // K bytes per stage row (one SW128 atom)
+constexpr int kOperandBytes = kTile * kChunkBytes;  // 16 KB per operand per stage
+constexpr int kThreads = 192;
+constexpr long long kBudget = 4000000000ll;
+constexpr uint32_t kTmemCols = 256;
+
+struct TcArgs {
+  CUtensorMap ymap;       // 2D (ld, rows) map, box (128 bytes of K, 128 rows), SW128
+  const float *rs;        // per-row scales (E4M3) or null
+  float *G;
+  unsigned *flag;
+  int64_t nouter, rows, b, n, ld;
+  int s, dt, nk;          // nk: K chunks
+};
+
+// ---- PTX wrappers (tcgen05 / TMEM) -------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               ::"r"(dst_smem), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+               ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(bar) : "memory");
+}
+
+template <int DT> __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc,
+                                                         uint64_t bdesc, uint32_t idesc,
+                                                         uint32_t accum) {
+  if (DT == GLM_TF32) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+  } else if (DT == GLM_E4M3) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+  }
+}
+
+// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart (SBO), version 1 (sm_100+).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // LBO (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // SBO
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // layout: SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D FP32, A/B K-major, M = N = 128.
+template <int DT> __host__ __device__ constexpr uint32_t instr_desc() {
+  // operand format field: kind::f16 -> F16 0 / BF16 1; kind::tf32 -> 2;
+  // kind::f8f6f4 -> E4M3 0
+  return (1u << 4)                                                      // D = F32
+         | ((uint32_t)(DT == GLM_BF16 ? 1 : DT == GLM_TF32 ? 2 : 0) << 7)  // A format
+         | ((uint32_t)(DT == GLM_BF16 ? 1 : DT == GLM_TF32 ? 2 : 0) << 10) // B format
+         | ((uint32_t)(kTile >> 3) << 17)                               // N >> 3
+         | ((uint32_t)(kTile >> 4) << 24);                              // M >> 4
+}
+
+// Output tile t of the flattened (outer step, lower-triangular tile pair)
+// list; returns false when the tile holds no strictly-lower block entry.
+struct Tile {
+  int64_t g, tj, ti, rows_g;
+};
+__device__ __forceinline__ bool tile_at(const TcArgs &a, int64_t T, int64_t P, int64_t t,
+                                        Tile &o) {
+  const int64_t sb = (int64_t)a.s * a.b;
+  o.g = t / P;
+  const int64_t p = t - o.g * P;
+  int64_t tj = (int64_t)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+  while (tj * (tj + 1) / 2 > p) --tj;
+  while ((tj + 1) * (tj + 2) / 2 <= p) ++tj;
+  o.tj = tj;
+  o.ti = p - tj * (tj + 1) / 2;
+  o.rows_g = min(sb, a.rows - o.g * sb);
+  const int64_t r0 = o.tj * kTile, c0 = o.ti * kTile;
+  const int64_t r_last = min(r0 + kTile, o.rows_g) - 1;
+  return r_last >= r0 && r_last / a.b > c0 / a.b;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_gram_tc(const __grid_constant__ TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t sbase0 = smem_u32(smem_raw);
+  unsigned char *smem = smem_raw + (round_up(sbase0, 1024) - sbase0);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t stage_a = sbase;                                  // + st * 32 KB
+  const uint32_t bars = sbase + kStages * 2 * kOperandBytes;       // 8-byte barriers
+  const uint32_t full0 = bars, empty0 = bars + 8 * kStages;
+  const uint32_t tfull0 = bars + 16 * kStages, tempty0 = tfull0 + 16;
+  const uint32_t drain = tempty0 + 16;        // MMA unwind barrier
+  const uint32_t tmem_slot = drain + 16;      // 16-byte aligned TMEM address slot
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull0 + 8 * i, 1);
+      mbar_init(tempty0 + 8 * i, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem + (tmem_slot - sbase));
+
+  const int64_t sb = (int64_t)a.s * a.b;
+  const int64_t T = (sb + kTile - 1) / kTile;
+  const int64_t P = T * (T + 1) / 2;
+  const int64_t ntiles = a.nouter * P;
+  volatile int *vabort = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int64_t it = 0;
+      for (int64_t t = blockIdx.x; t < ntiles && !*vabort; t += gridDim.x) {
+        Tile tl;
+        if (!tile_at(a, T, P, t, tl)) continue;
+        const int32_t ya = (int32_t)(tl.g * sb + tl.tj * kTile);
+        const int32_t yb = (int32_t)(tl.g * sb + tl.ti * kTile);
+        for (int kc = 0; kc < a.nk; ++kc, ++it) {
+          const int st = (int)(it % kStages);
+          if (it >= kStages &&
+              !mbar_wait_bounded(empty0 + 8 * st, (uint32_t)((it / kStages - 1) & 1), kBudget)) {
+            atomicOr(&s_abort, 1);
+            break;
+          }
+          const uint32_t full = full0 + 8 * st;
+          mbar_arrive_expect_tx(full, 2 * kOperandBytes);
+          const int32_t xk = kc * (kChunkBytes / elem_bytes(DT));
+          const uint32_t dA = stage_a + st * 2 * kOperandBytes;
+          tma_load_2d(dA, &a.ymap, xk, ya, full);
+          tma_load_2d(dA + kOperandBytes, &a.ymap, xk, yb, full);
+        }
+      }
+      // unwind: wait (bounded) for the loads still in flight
+      if (*vabort)
+        for (int64_t i = (it > kStages ? it - kStages : 0); i < it; ++i)
+          mbar_wait_bounded(full0 + 8 * (i % kStages), (uint32_t)((i / kStages) & 1), kBudget);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc<DT>();
+      int64_t it = 0, tc = 0;
+      for (int64_t t = blockIdx.x; t < ntiles && !*vabort; t += gridDim.x) {
+        Tile tl;
+        if (!tile_at(a, T, P, t, tl)) continue;
+        const int buf = (int)(tc & 1);
+        if (tc >= 2 &&
+            !mbar_wait_bounded(tempty0 + 8 * buf, (uint32_t)((tc / 2 - 1) & 1), kBudget)) {
+          atomicOr(&s_abort, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tmem_d = tmem_base + (uint32_t)(buf * kTile);
+        bool ok = true;
+        for (int kc = 0; kc < a.nk; ++kc, ++it) {
+          const int st = (int)(it % kStages);
+          if (!mbar_wait_bounded(full0 + 8 * st, (uint32_t)((it / kStages) & 1), kBudget)) {
+            atomicOr(&s_abort, 1);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = stage_a + st * 2 * kOperandBytes;
+          const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + kOperandBytes);
+#pragma unroll
+          for (int k = 0; k < kChunkBytes / 32; ++k)  // 32 bytes of K per MMA
+            tc_mma<DT>(tmem_d, da + 2 * k, db + 2 * k, idesc, (kc | k) != 0);
+          tc_commit(empty0 + 8 * st);  // stage free once these MMAs have read it
+        }
+        if (!ok) break;
+        tc_commit(tfull0 + 8 * buf);   // accumulator ready for the epilogue
+        ++tc;
+      }
+      // unwind: make sure no MMA issued here is still running before TMEM is freed
+      if (*vabort) {
+        tc_commit(drain);
+        mbar_wait_bounded(drain, 0, kBudget);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quad = warp & 3;  // TMEM lanes 32*quad .. 32*quad+31
+    int64_t tc = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      Tile tl;
+      if (!tile_at(a, T, P, t, tl)) continue;
+      const int buf = (int)(tc & 1);
+      if (!mbar_wait_bounded(tfull0 + 8 * buf, (uint32_t)((tc / 2) & 1), kBudget)) {
+        atomicOr(&s_abort, 1);
+        break;
+      }
+      tc_fence_after();
+      const int64_t rho = tl.tj * kTile + quad * 32 + lane;  // this thread's row
+      const int64_t j = rho / a.b, l = rho - j * a.b;
+      const bool row_ok = rho < tl.rows_g;
+      const int64_t limit = j * a.b;                           // columns < j b
+      float *grow = a.G + tl.g * gram_size(a.s, a.b) + gram_off(j, a.b) + l * gram_ld(j, a.b);
+      const float srow = (DT == GLM_E4M3 && row_ok) ? a.rs[tl.g * sb + rho] : 1.f;
+#pragma unroll 1
+      for (int cc = 0; cc < kTile / 32; ++cc) {
+        float v[32];
+        tmem_ld32(tmem_base + (uint32_t)(buf * kTile + cc * 32) + ((uint32_t)(quad * 32) << 16),
+                  v);
+        const int64_t c0 = tl.ti * kTile + cc * 32;
+        if (!row_ok || c0 >= limit) continue;
+        if (DT == GLM_E4M3) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            v[i] *= srow * ((c0 + i < limit) ? __ldg(a.rs + tl.g * sb + c0 + i) : 0.f);
+        }
+        if (c0 + 32 <= limit) {
+          float4 *d = reinterpret_cast<float4 *>(grow + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < limit) grow[c0 + i] = v[i];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+      ++tc;
+    }
+  }
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0 && a.flag) atomicOr(a.flag, FLAG_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+}  // namespace
 
 bool gram_tc_supported(int dt, int64_t ld) {
-  (void)dt;
-  (void)ld;
+  if (dt == GLM_E4M3) return ld % 128 == 0;
+  if (dt == GLM_BF16 || dt == GLM_F16 || dt == GLM_TF32) return ld % 64 == 0;
   return false;
 }
 
-int launch_gram_tc(const GramArgs &a, cudaStream_t st) {
-  (void)a;
-  (void)st;
-  return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram not built");
+int launch_gram_tc(const GramArgs &g, cudaStream_t st) {
+  if (g.s < 2 || g.nouter <= 0) return GLM_OK;
+  if (!gram_tc_supported(g.dt, g.ld))
+    return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram: unsupported operand type or ld");
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  const int eb = elem_bytes(g.dt);
+  GLM_TRY(make_tmap_2d_sw128(&a.ymap, g.Y, g.dt, (uint64_t)g.ld,
+                             (uint64_t)g.nouter * g.s * g.b, (uint64_t)g.ld * eb,
+                             (uint32_t)(kChunkBytes / eb), (uint32_t)kTile));
+  a.rs = g.rs;
+  a.G = g.G;
+  a.flag = g.flag;
+  a.nouter = g.nouter;
+  a.rows = g.rows;
+  a.b = g.b;
+  a.n = g.n;
+  a.ld = g.ld;
+  a.s = g.s;
+  a.dt = g.dt;
+  a.nk = (int)((g.n * eb + kChunkBytes - 1) / kChunkBytes);  // K chunks covering n
+  const int64_t sb = (int64_t)g.s * g.b;
+  const int64_t T = (sb + kTile - 1) / kTile;
+  const int64_t ntiles = g.nouter * T * (T + 1) / 2;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  const size_t smem = 1024 + kStages * 2 * kOperandBytes + 8 * (2 * kStages + 6) + 32;
+  void (*kern)(TcArgs);
+  switch (g.dt) {
+  case GLM_BF16: kern = k_gram_tc<GLM_BF16>; break;
+  case GLM_F16: kern = k_gram_tc<GLM_F16>; break;
+  case GLM_TF32: kern = k_gram_tc<GLM_TF32>; break;
+  default: kern = k_gram_tc<GLM_E4M3>; break;
+  }
+  GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, kThreads, smem, st>>>(a);
+  GLM_CUDA_TRY(cudaGetLastError());
+  return GLM_OK;
 }
 
 }  // namespace glm
