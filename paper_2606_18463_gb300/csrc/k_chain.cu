@@ -350,8 +350,12 @@ k_chain(const __grid_constant__ ChainArgs a) {
     const float *labs;
     if (staged) {
       const int slot = h % ns;
-      if (!mbar_wait_bounded(full_y0 + 8 * slot, (uint32_t)((h / ns) & 1), kWaitBudget))
+      // one thread polls; the others park on the named barrier (spinning
+      // warps would steal issue slots from the critical path)
+      if (tid == 0 &&
+          !mbar_wait_bounded(full_y0 + 8 * slot, (uint32_t)((h / ns) & 1), kWaitBudget))
         atomicOr(&s_abort, 1);
+      csync();
       Ys = reinterpret_cast<const TY *>(ybuf + (int64_t)slot * L.yslot);
       ystride = nc;
       labs = reinterpret_cast<const float *>(ybuf + (int64_t)slot * L.yslot + L.ylab_off);
@@ -380,7 +384,10 @@ k_chain(const __grid_constant__ ChainArgs a) {
         Raw8<TY> raw[kRows];
 #pragma unroll
         for (int u = 0; u < kRows; ++u) {
-          if (r0 + u < R && colok) raw[u].load(Ys + (r0 + u) * ystride + col, staged);
+          // odd groups read their rows in the order 1,0,3,2 so that one load
+          // instruction touches rows of both parities (both bank halves)
+          const int64_t r = r0 + (u ^ (gi & 1));
+          if (r < R && colok) raw[u].load(Ys + r * ystride + col, staged);
           else raw[u].zero();
         }
 #pragma unroll
@@ -390,6 +397,10 @@ k_chain(const __grid_constant__ ChainArgs a) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) acc[u] = fmaf(f[i], xv[i], acc[u]);
         }
+      }
+      if (gi & 1) {  // undo the read order: acc[u] holds row r0 + (u ^ 1)
+        float t0 = acc[0]; acc[0] = acc[1]; acc[1] = t0;
+        float t2 = acc[2]; acc[2] = acc[3]; acc[3] = t2;
       }
 #pragma unroll
       for (int u = 0; u < kRows; ++u)
@@ -417,30 +428,30 @@ k_chain(const __grid_constant__ ChainArgs a) {
         }
       }
     }
-    if (!mbar_wait_bounded(bar_r, h & 1, kWaitBudget)) atomicOr(&s_abort, 1);
+    if (tid == 0 && !mbar_wait_bounded(bar_r, h & 1, kWaitBudget)) atomicOr(&s_abort, 1);
     csync();
     if (s_abort) { abort = true; break; }
 
     // ---- C: own rows' margins (C-way shuffle trees, fixed order) and labels --
-    {
-      const int per = kCThreads / C;
-      const int e_local = tid / C, src = tid - (tid / C) * C;
-      for (int e0 = 0; e0 < sh * nown; e0 += per) {
-        const int e = e0 + e_local;
-        TR v = 0;
-        if (e < sh * nown) {
-          const int j = e / nown, ll = e - j * nown;
-          v = (TR)rrecv[((int64_t)src * s + j) * rpb + ll];
-        }
-        for (int off = C / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (src == 0 && e < sh * nown) {
-          const int j = e / nown, ll = e - j * nown;
-          rown[j * rpb + ll] = v;
-          yown[j * rpb + ll] = labs[(int64_t)j * b + l0 + ll];
-        }
+    // entries across lanes (consecutive shared addresses), sources summed in a
+    // fixed order with four independent partial sums
+    for (int e = tid; e < sh * nown; e += kCThreads) {
+      const int j = e / nown, ll = e - j * nown;
+      const float *col = rrecv + (int64_t)j * rpb + ll;
+      const int64_t str = (int64_t)s * rpb;
+      TR p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+      int src = 0;
+      for (; src + 4 <= C; src += 4) {
+        p0 += (TR)col[(src + 0) * str];
+        p1 += (TR)col[(src + 1) * str];
+        p2 += (TR)col[(src + 2) * str];
+        p3 += (TR)col[(src + 3) * str];
       }
+      for (; src < C; ++src) p0 += (TR)col[src * str];
+      rown[j * rpb + ll] = (p0 + p1) + (p2 + p3);
+      yown[j * rpb + ll] = labs[(int64_t)j * b + l0 + ll];
     }
-    if (gmode == G_STEP && sh >= 2) {
+    if (gmode == G_STEP && sh >= 2 && tid == 0) {
       if (!mbar_wait_bounded(full_g0 + 8 * (h & 1), (uint32_t)((h >> 1) & 1), kWaitBudget))
         atomicOr(&s_abort, 1);
     }
@@ -459,9 +470,10 @@ k_chain(const __grid_constant__ ChainArgs a) {
           gsrc = gbuf + (h & 1) * L.gslot_floats + goff;
           goff += (int64_t)rpb * ldj;
         } else if (gmode == G_BLOCK) {
-          if (!mbar_wait_bounded(full_g0 + 8 * (kblk & 1), (uint32_t)((kblk >> 1) & 1),
-                                 kWaitBudget))
+          if (tid == 0 && !mbar_wait_bounded(full_g0 + 8 * (kblk & 1),
+                                             (uint32_t)((kblk >> 1) & 1), kWaitBudget))
             atomicOr(&s_abort, 1);
+          csync();
           gsrc = gbuf + (kblk & 1) * L.gslot_floats;
         } else {
           gsrc = Gh + gram_off(j, b) + l0 * ldj;
@@ -543,7 +555,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
         }
       }
       if (tid == 0) mbar_arrive_expect_tx(bar_u0 + 8 * (J & 1), (uint32_t)(b * sizeof(TR)));
-      if (!mbar_wait_bounded(bar_u0 + 8 * (J & 1), (J >> 1) & 1, kWaitBudget))
+      if (tid == 0 && !mbar_wait_bounded(bar_u0 + 8 * (J & 1), (J >> 1) & 1, kWaitBudget))
         atomicOr(&s_abort, 1);
       ++J;
       csync();
@@ -592,8 +604,9 @@ k_chain(const __grid_constant__ ChainArgs a) {
         }
       }
       if (g < RG) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) part[(int64_t)g * nc + col + i] = acc[i];
+        float4 *pp = reinterpret_cast<float4 *>(part + (int64_t)g * nc + col);
+        pp[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        pp[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
       }
       csync();
       if (staged && tid == 0) mbar_arrive(empty_y0 + 8 * (h % ns));  // Y slot free again
