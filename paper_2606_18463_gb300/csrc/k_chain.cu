@@ -52,7 +52,7 @@ struct Layout {
   int64_t gslot_floats;    // floats per G slot (two slots)
   int64_t ylab_off;        // byte offset of the labels inside a Y slot
   int64_t yslot;           // bytes per Y slot
-  size_t off_uh, off_rrecv, off_rown, off_yown, off_red, off_part, off_bar, off_coef,
+  size_t off_uh, off_rrecv, off_rown, off_yown, off_part, off_bar, off_coef,
       off_rem, off_gbuf, off_ybuf, total;
 };
 
@@ -78,7 +78,6 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t b, int s, int C
   L.off_rrecv = take((size_t)C * s * L.rpb * 4, 16);
   L.off_rown = take((size_t)s * L.rpb * tr_bytes, 16);
   L.off_yown = take((size_t)s * L.rpb * 4, 16);
-  L.off_red = take((size_t)(L.rpb > kCWarps ? L.rpb : kCWarps) * tr_bytes, 16);
   L.off_part = take((size_t)kCThreads * 8 * 4, 16);
   L.off_bar = take(16 * 8, 16);
   L.off_coef = take((size_t)3 * (s + 1) * tr_bytes, 16);  // c^j, c^-j, alpha c^(j-1)
@@ -170,6 +169,33 @@ template <> struct Raw8<__half> {
 
 constexpr int kRows = 4;  // consecutive rows per thread group in the margin
 
+// Lane-strided dot product of one G row with the residual history over
+// [0, jb), four independent partial sums in a fixed order.  Instantiated once
+// for staged rows (shared memory) and once for rows read from global memory,
+// so each instance uses a single address space.
+template <typename TR, bool kShared>
+__device__ __forceinline__ TR row_dot(const float *__restrict__ grow,
+                                      const TR *__restrict__ uh, int jb, int lane) {
+  TR a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int c = lane;
+#pragma unroll 2
+  for (; c + 96 < jb; c += 128) {
+    float g0, g1, g2, g3;
+    if (kShared) {
+      g0 = grow[c]; g1 = grow[c + 32]; g2 = grow[c + 64]; g3 = grow[c + 96];
+    } else {
+      g0 = __ldg(grow + c); g1 = __ldg(grow + c + 32);
+      g2 = __ldg(grow + c + 64); g3 = __ldg(grow + c + 96);
+    }
+    a0 += (TR)g0 * uh[c];
+    a1 += (TR)g1 * uh[c + 32];
+    a2 += (TR)g2 * uh[c + 64];
+    a3 += (TR)g3 * uh[c + 96];
+  }
+  for (; c < jb; c += 32) a0 += (TR)(kShared ? grow[c] : __ldg(grow + c)) * uh[c];
+  return (a0 + a1) + (a2 + a3);
+}
+
 __device__ __forceinline__ void csync() { named_sync(1, kCThreads); }
 
 template <typename TY, typename TR>
@@ -194,7 +220,6 @@ k_chain(const __grid_constant__ ChainArgs a) {
   float *rrecv = reinterpret_cast<float *>(smem + L.off_rrecv);
   TR *rown = reinterpret_cast<TR *>(smem + L.off_rown);
   float *yown = reinterpret_cast<float *>(smem + L.off_yown);
-  TR *red = reinterpret_cast<TR *>(smem + L.off_red);
   float *part = reinterpret_cast<float *>(smem + L.off_part);
   float *gbuf = reinterpret_cast<float *>(smem + L.off_gbuf);
   const uint32_t sbase = smem_u32(smem);
@@ -244,7 +269,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
         const int shh = (hh == a.nouter - 1) ? a.s_last : s;
         if (ns) {
           const int slot = hh % ns;
-          if (hh >= ns && !mbar_wait_bounded(empty_y0 + 8 * slot,
+          if (hh >= ns && !mbar_wait_sleep(empty_y0 + 8 * slot,
                                              (uint32_t)((hh / ns - 1) & 1), kWaitBudget)) {
             atomicOr(&s_abort, 1);
             break;
@@ -262,7 +287,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
         }
         if (gmode == G_STEP && shh >= 2) {
           const int slot = hh & 1;
-          if (hh >= 2 && !mbar_wait_bounded(empty_g0 + 8 * slot,
+          if (hh >= 2 && !mbar_wait_sleep(empty_g0 + 8 * slot,
                                             (uint32_t)(((hh >> 1) - 1) & 1), kWaitBudget)) {
             atomicOr(&s_abort, 1);
             break;
@@ -286,7 +311,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
           bool stop = false;
           for (int j = 1; j < shh; ++j, ++kblk) {
             const int slot = (int)(kblk & 1);
-            if (kblk >= 2 && !mbar_wait_bounded(empty_g0 + 8 * slot,
+            if (kblk >= 2 && !mbar_wait_sleep(empty_g0 + 8 * slot,
                                                 (uint32_t)(((kblk >> 1) - 1) & 1), kWaitBudget)) {
               atomicOr(&s_abort, 1);
               stop = true;
@@ -328,9 +353,6 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const int groups = kCThreads / tpr; // row groups (kRows consecutive rows each)
   const int gi = tid / tpr, li = tid % tpr;
   const bool vsend_r = (b % 4 == 0) && (rpb % 4 == 0);            // 4 rows -> one v4
-  const bool vsend_u = sizeof(TR) == 4 ? (b % 4 == 0 && rpb % 4 == 0)
-                                       : (b % 2 == 0 && rpb % 2 == 0);
-  const int upk = sizeof(TR) == 4 ? 4 : 2;                        // values per vector send
   const int loss_kind = a.loss;
   unsigned *const flag = a.flag;
   const TY *Y = static_cast<const TY *>(a.Y);
@@ -458,110 +480,67 @@ k_chain(const __grid_constant__ ChainArgs a) {
     csync();
     if (s_abort) { abort = true; break; }
 
-    // ---- D: inner s-step recurrence -----------------------------------------
-    const int wpr = nown > 0 ? max(1, kCWarps / nown) : 1;
-    int64_t goff = 0;   // floats into the G_STEP slot
-    for (int j = 0; j < sh; ++j) {
-      if (j > 0) {
-        const int64_t jb = (int64_t)j * b;
+    // ---- D: inner s-step recurrence (row warps only) ------------------------
+    // Only the warps that own rows run the serial loop and synchronise on
+    // named barrier 2; the other consumer warps park at the barrier below for
+    // the whole recurrence, so they take no issue slots from the critical path.
+    const int nrw = nown < kCWarps ? nown : kCWarps;
+    if (warp < nrw) {
+      int64_t goff = 0;   // floats into the G_STEP slot
+      for (int j = 0; j < sh; ++j) {
         const int64_t ldj = gram_ld(j, b);
-        const float *gsrc;
-        if (gmode == G_STEP) {
-          gsrc = gbuf + (h & 1) * L.gslot_floats + goff;
-          goff += (int64_t)rpb * ldj;
-        } else if (gmode == G_BLOCK) {
-          if (tid == 0 && !mbar_wait_bounded(full_g0 + 8 * (kblk & 1),
-                                             (uint32_t)((kblk >> 1) & 1), kWaitBudget))
-            atomicOr(&s_abort, 1);
-          csync();
-          gsrc = gbuf + (kblk & 1) * L.gslot_floats;
-        } else {
-          gsrc = Gh + gram_off(j, b) + l0 * ldj;
-        }
-        for (int item = warp; item < nown * wpr; item += kCWarps) {
-          const int rr = item / wpr, pp = item - rr * wpr;
-          const float *grow = gsrc + rr * ldj;
-          TR acc0 = 0, acc1 = 0;
-          int64_t c = (int64_t)pp * 32 + lane;
-          const int64_t step = 32 * (int64_t)wpr;
-          for (; c + step < jb; c += 2 * step) {
-            acc0 += (TR)grow[c] * uh[c];
-            acc1 += (TR)grow[c + step] * uh[c + step];
+        int64_t gofs = 0;  // float offset of this block row's own rows
+        if (j > 0) {
+          if (gmode == G_STEP) {
+            gofs = (h & 1) * L.gslot_floats + goff;
+            goff += (int64_t)rpb * ldj;
+          } else if (gmode == G_BLOCK) {
+            if (tid == 0 && !mbar_wait_bounded(full_g0 + 8 * (kblk & 1),
+                                               (uint32_t)((kblk >> 1) & 1), kWaitBudget))
+              atomicOr(&s_abort, 1);
+            named_sync(2, nrw * 32);
+            gofs = (kblk & 1) * L.gslot_floats;
+          } else {
+            gofs = gram_off(j, b) + l0 * ldj;
           }
-          if (c < jb) acc0 += (TR)grow[c] * uh[c];
-          TR acc = acc0 + acc1;
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-          if (lane == 0) red[item] = acc;
         }
-        csync();
-        if (gmode == G_BLOCK) {
+        // one warp per own row: correction dot product (4 independent partial
+        // sums, fixed order), shuffle-tree total in every lane, residual, and a
+        // lane-parallel fan-out of c^{-j} u to the C CTAs (one instruction)
+        const int jb = (int)(j * b);
+        const uint32_t ubar = 8 * (J & 1);
+        for (int rr = warp; rr < nown; rr += nrw) {
+          TR corr = 0;
+          if (j > 0) {
+            corr = gmode != G_NONE
+                       ? row_dot<TR, true>(gbuf + gofs + rr * ldj, uh, jb, lane)
+                       : row_dot<TR, false>(Gh + gofs + rr * ldj, uh, jb, lane);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) corr += __shfl_xor_sync(0xffffffffu, corr, off);
+          }
+          const TR z = cpw[j] * rown[j * rpb + rr] - zcw[j] * corr;
+          const TR u = dloss<TR>(loss_kind, z, (TR)yown[j * rpb + rr]);
+          if (lane == 0 && (!isfinite(z) || !isfinite(u))) atomicOr(flag, FLAG_NONFINITE);
+          const TR uw = u * cinw[j];
+          const uint32_t offu = (uint32_t)(((int64_t)j * b + l0 + rr) * sizeof(TR));
+          for (int d = lane; d < C; d += 32) st_async(rem[32 + d] + offu, uw, rem[48 + d] + ubar);
+        }
+        if (tid == 0) {
+          mbar_arrive_expect_tx(bar_u0 + 8 * (J & 1), (uint32_t)(b * sizeof(TR)));
+          if (!mbar_wait_bounded(bar_u0 + 8 * (J & 1), (J >> 1) & 1, kWaitBudget))
+            atomicOr(&s_abort, 1);
+        }
+        ++J;
+        named_sync(2, nrw * 32);
+        if (gmode == G_BLOCK && j > 0) {  // every row warp is done with this G block row
           if (tid == 0) mbar_arrive(empty_g0 + 8 * (kblk & 1));
           ++kblk;
         }
+        if (s_abort) break;
       }
-      if (warp == 0) {
-        // residuals of the own rows (lanes < nown), then warp 0 fans the
-        // sends out across its lanes (16-byte vectors when aligned)
-        for (int rb0 = 0; rb0 < nown; rb0 += 32) {
-          const int rr = rb0 + lane;
-          TR uw = 0;
-          if (rr < nown) {
-            TR corr = 0;
-            if (j > 0)
-              for (int p = 0; p < wpr; ++p) corr += red[rr * wpr + p];
-            const TR z = cpw[j] * rown[j * rpb + rr] - zcw[j] * corr;
-            const TR u = dloss<TR>(loss_kind, z, (TR)yown[j * rpb + rr]);
-            if (!isfinite(z) || !isfinite(u)) atomicOr(flag, FLAG_NONFINITE);
-            uw = u * cinw[j];
-          }
-          const int nrow = min(32, nown - rb0);
-          const uint32_t ubase = (uint32_t)(((int64_t)j * b + l0 + rb0) * sizeof(TR));
-          const uint32_t ubar = 8 * (J & 1);
-          if (vsend_u) {
-            const int cnt = (nrow / upk) * C;
-            for (int t0 = 0; t0 < cnt; t0 += 32) {
-              const int t = t0 + lane;
-              const int chunk = (t < cnt) ? t / C : 0;
-              const int d = t - chunk * C;
-              if (sizeof(TR) == 4) {
-                const float v0 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk);
-                const float v1 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk + 1);
-                const float v2 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk + 2);
-                const float v3 = __shfl_sync(0xffffffffu, (float)uw, 4 * chunk + 3);
-                if (t < cnt)
-                  st_async_v4(rem[32 + d] + ubase + 16 * chunk, v0, v1, v2, v3,
-                              rem[48 + d] + ubar);
-              } else {
-                const double v0 = __shfl_sync(0xffffffffu, (double)uw, 2 * chunk);
-                const double v1 = __shfl_sync(0xffffffffu, (double)uw, 2 * chunk + 1);
-                if (t < cnt)
-                  st_async_v2(rem[32 + d] + ubase + 16 * chunk, v0, v1, rem[48 + d] + ubar);
-              }
-            }
-          } else {
-            const int cnt = nrow * C;
-            for (int t0 = 0; t0 < cnt; t0 += 32) {
-              const int t = t0 + lane;
-              const int src_lane = (t < cnt) ? t / C : 0;
-              const TR v = __shfl_sync(0xffffffffu, uw, src_lane);
-              if (t < cnt) {
-                const int d = t - src_lane * C;
-                st_async(rem[32 + d] + ubase + (uint32_t)(src_lane * sizeof(TR)), v,
-                         rem[48 + d] + ubar);
-              }
-            }
-          }
-        }
-      }
-      if (tid == 0) mbar_arrive_expect_tx(bar_u0 + 8 * (J & 1), (uint32_t)(b * sizeof(TR)));
-      if (tid == 0 && !mbar_wait_bounded(bar_u0 + 8 * (J & 1), (J >> 1) & 1, kWaitBudget))
-        atomicOr(&s_abort, 1);
-      ++J;
-      csync();
-      if (s_abort) { abort = true; break; }
     }
-    if (abort) break;
+    csync();
+    if (s_abort) { abort = true; break; }
     if (gmode == G_STEP && sh >= 2 && tid == 0) mbar_arrive(empty_g0 + 8 * (h & 1));
 
     // ---- E: x <- c^{sh} x - alpha c^{sh-1} Y^T (c^{-j} u), own slice ---------
