@@ -207,6 +207,21 @@ int glm_loss(glm_handle h, const float *x, float lambda, double *out);
 int glm_sample_indices(uint64_t seed, uint32_t problem, int64_t first_draw,
                        int64_t count, int64_t m, int32_t *out);
 
+/*
+ * No counterpart in the paper: a form of glm_sample_indices for a HOST
+ * output that allocates nothing.  The draws are staged in a fixed device
+ * array of GLM_SAMPLE_NOALLOC_MAX int32 (4 MiB, one per device) instead of a
+ * per-call cudaMalloc/cudaFree; results equal glm_sample_indices'.
+ * out: host int32[count].  count > GLM_SAMPLE_NOALLOC_MAX returns GLM_EINVAL
+ * before any device work.  Calls whose work overlaps on the same GPU race on
+ * the shared staging array: serialise them.  The first call on a device
+ * resolves the array's address (cudaGetSymbolAddress, with that device
+ * current): make it before any stream capture.  Blocks.
+ */
+#define GLM_SAMPLE_NOALLOC_MAX 1048576
+int glm_sample_indices_noalloc(uint64_t seed, uint32_t problem, int64_t first_draw,
+                               int64_t count, int64_t m, int32_t *out);
+
 /* ---- kernel-level entry points (tests, micro-benchmarks) ----------------- */
 
 /*

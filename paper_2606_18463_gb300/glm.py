@@ -36,7 +36,7 @@ EXPORTED = [
     "glm_create_ex", "glm_destroy", "glm_shape", "glm_stream", "glm_sync",
     "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_ca_sgd_run",
     "glm_ca_sgd_run_ex", "glm_ca_plan", "glm_kernel_times", "glm_loss",
-    "glm_sample_indices", "glm_gram_lower",
+    "glm_sample_indices", "glm_sample_indices_noalloc", "glm_gram_lower",
     "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
     "glm_batch_choice", "glm_batch_destroy",
 ]
@@ -123,6 +123,7 @@ def load():
                                   ctypes.POINTER(i64)], i32),
             "glm_loss": ([vp, vp, f32, ctypes.POINTER(ctypes.c_double)], i32),
             "glm_sample_indices": ([u64, ctypes.c_uint32, i64, i64, i64, vp], i32),
+            "glm_sample_indices_noalloc": ([u64, ctypes.c_uint32, i64, i64, i64, vp], i32),
             "glm_gram_lower": ([vp, i32, i64, i32, i64, i64, i64, vp, vp, i32, vp], i32),
             "glm_batch_opts_default": ([ctypes.POINTER(glm_batch_opts)], None),
             "glm_batch_create": ([i32, ctypes.POINTER(glm_problem_desc),
@@ -226,6 +227,18 @@ def glm_loss(h, x, lam) -> float:
 
 def glm_sample_indices(seed, problem, first_draw, count, m, out) -> None:
     _check(load().glm_sample_indices(seed, problem, first_draw, count, m, _ptr(out)))
+
+
+def glm_sample_indices_noalloc(seed, problem, first_draw, count, m, out) -> None:
+    """Host-output index draw staged in a fixed device array (no allocation).
+
+    out: host int32 buffer (numpy array) of at least `count` entries;
+    count <= GLM_SAMPLE_NOALLOC_MAX.
+    """
+    _check(load().glm_sample_indices_noalloc(seed, problem, first_draw, count, m, _ptr(out)))
+
+
+GLM_SAMPLE_NOALLOC_MAX = 1 << 20
 
 
 def glm_gram_lower(Y, dtype, nouter, s, b, n, ld, row_scale, G, impl=0, stream=None) -> None:
