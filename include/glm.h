@@ -241,18 +241,26 @@ int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b,
                    int impl, void *stream);
 
 /* ---- batched fits -------------------------------------------------------- */
-
+/*
+ * No counterpart in the paper (its experiments fit one problem at a time):
+ * many independent fits of uneven m, n and lambda share the device.  Every
+ * problem is fit with CA-SGD (paper Algorithm 1) on its own index stream:
+ * problem p draws from Philox key (desc[p].seed, p), so it reproduces a
+ * single-problem run with glm_ca_opts.problem = p.
+ */
 typedef struct {
   const void *A;     /* m x n, element type input_dtype, host or device    */
   const float *y;    /* m labels                                           */
-  int64_t m, n;
+  int64_t m, n;      /* 1 <= m < 2^31, 1 <= n <= 16384                     */
   int loss;          /* GLM_LOGISTIC or GLM_LSQ                            */
   float lambda, eta;
-  int64_t iters;     /* SGD-equivalent iterations                          */
+  int64_t iters;     /* SGD-equivalent iterations (0: the problem is idle) */
   uint64_t seed;
-  int s;             /* 0: chosen by the autotuner                         */
-  int64_t b;         /* mini-batch size (required)                         */
-  int gram_dtype;    /* -1: chosen by the autotuner                        */
+  int s;             /* 1..64, or 0: chosen by the autotuner (4, 8 or 16)  */
+  int64_t b;         /* mini-batch size, 1..1024, s*b <= 8192 (required:
+                        b is part of the problem, the tuner never picks it) */
+  int gram_dtype;    /* -1: the storage type; else GLM_F32, GLM_TF32,
+                        GLM_BF16 or GLM_F16, the same for every problem     */
 } glm_problem_desc;
 
 typedef struct glm_batch_s *glm_batch;
@@ -266,22 +274,35 @@ typedef struct {
 
 void glm_batch_opts_default(glm_batch_opts *o);
 
-/* Upload P independent problems.  Blocks. */
+/*
+ * Upload P independent problems (each converted like glm_create_ex, with
+ * per-column scales) and run the autotuner for every problem with s = 0: for
+ * each n among them it times one round of s in {4, 8, 16} on up to 32 of those
+ * problems (scratch iterates) and keeps the fastest in samples per second.
+ * The tuner only chooses what leaves the exact-arithmetic iterate unchanged
+ * (s; CA-SGD equals SGD for every s), never b or the operand precision.
+ * Returns GLM_EINVAL on a bad descriptor (the message names the problem).
+ * Blocks.
+ */
 int glm_batch_create(int P, const glm_problem_desc *descs,
                      const glm_batch_opts *opts, glm_batch *out);
 
 /*
- * Run every problem's CA-SGD fit in one persistent launch: CTAs take
- * problems from a device work queue (longest first).  xs: host array of P
- * device FP32[n_p] pointers, in/out.  status: host int[P] or NULL, filled
- * with per-problem GLM_OK / GLM_ENONFINITE after completion.  Blocks.
+ * Run every problem's fit.  The run proceeds in rounds of K outer steps of
+ * every problem: one gather launch, one Gram launch per group of problems
+ * sharing (s, b, n), and one persistent chain launch whose CTAs take problems
+ * from a device work queue, longest first; all rounds are captured once as a
+ * CUDA graph and replayed by later runs.  xs: host array of P device FP32[n_p]
+ * pointers, read as x0 and written with x_T.  status: host int[P] or NULL,
+ * filled with GLM_OK or GLM_ENONFINITE per problem (flags are then cleared).
+ * Blocks.
  */
 int glm_batch_run(glm_batch bt, float *const *xs, int *status);
 
-/* Per-problem risk F_p(x_p) into host double[P].  Blocks. */
+/* Per-problem risk F_p(x_p) (as glm_loss) into host double[P].  Blocks. */
 int glm_batch_loss(glm_batch bt, float *const *xs, double *out);
 
-/* The (s, b, gram dtype, cluster) the autotuner chose for problem p. */
+/* The s, b and Gram operand type used for problem p. */
 int glm_batch_choice(glm_batch bt, int p, int *s, int64_t *b, int *gram_dtype);
 
 int glm_batch_destroy(glm_batch bt);

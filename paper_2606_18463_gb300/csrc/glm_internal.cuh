@@ -472,6 +472,30 @@ int launch_chain(const ChainArgs &a, cudaStream_t st);
 int chain_max_cluster(const ChainArgs &a);
 bool chain_cluster_ok(int C, int64_t b);
 
+// One problem of one round of a batched run (device table filled by the host).
+// The round covers `nouter` outer steps of s b gathered rows each (the last
+// one holds s_last b rows; the rest of its rows are zero).
+struct BatchItem {
+  const void *A; int64_t lda; const float *colscale; const float *y;  // storage
+  int64_t m; int n; int a_dt;
+  uint64_t seed, problem, q0;   // Philox key and first global draw of the round
+  int nouter, s, s_last, b;
+  void *Y; int y_dt; int64_t ldy;  // nouter * s * b gathered rows (Gram and GEMV operand)
+  float *lab;                      // nouter * s * b labels
+  float *G;                        // nouter * gram_size(s, b) floats (packed lower blocks)
+  float *x;                        // FP32[n] iterate, in/out
+  int loss, kahan;
+  float alpha;                     // eta / b
+  double c;                        // 1 - eta lambda
+  unsigned *flag;                  // the problem's device flag word
+};
+int launch_gather_batch(const BatchItem *items, int nitems, int64_t max_rows, cudaStream_t st,
+                        int a_dt);
+// Persistent chain over a work queue: CTAs take items order[0], order[1], ...
+// (*queue must be 0 on entry).  Every item of one launch has the same y_dt.
+int launch_chain_batch(const BatchItem *items, const int *order, int nitems, int *queue,
+                       int y_dt, int rec64, int max_n, int max_sb, int max_s, cudaStream_t st);
+
 int launch_loss(Handle *h, const float *x, float lambda, cudaStream_t st);
 int launch_sample(uint64_t seed, uint64_t problem, int64_t first, int64_t count,
                   int64_t m, int32_t *out, cudaStream_t st);

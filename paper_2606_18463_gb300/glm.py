@@ -323,3 +323,101 @@ class Dataset:
 
     def sync(self):
         _check(glm_sync(self.h))
+
+
+# ---- batched fits -------------------------------------------------------------
+def glm_batch_opts_default_struct() -> glm_batch_opts:
+    o = glm_batch_opts()
+    load().glm_batch_opts_default(ctypes.byref(o))
+    return o
+
+
+def glm_batch_create(P, descs, opts=None):
+    arr = (glm_problem_desc * P)(*descs)
+    out = ctypes.c_void_p()
+    _check(load().glm_batch_create(P, arr, ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(out)))
+    return out.value
+
+
+def glm_batch_run(bt, xs, status=None):
+    """xs: sequence of device FP32 iterates (torch tensors); returns the
+    per-problem status list (GLM_OK or GLM_ENONFINITE)."""
+    P = len(xs)
+    ptrs = (ctypes.c_void_p * P)(*[_ptr(x) for x in xs])
+    st = (ctypes.c_int * P)()
+    _check(load().glm_batch_run(bt, ptrs, st))
+    return list(st)
+
+
+def glm_batch_loss(bt, xs):
+    P = len(xs)
+    ptrs = (ctypes.c_void_p * P)(*[_ptr(x) for x in xs])
+    out = (ctypes.c_double * P)()
+    _check(load().glm_batch_loss(bt, ptrs, out))
+    return list(out)
+
+
+def glm_batch_choice(bt, p):
+    s, b, g = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+    _check(load().glm_batch_choice(bt, p, ctypes.byref(s), ctypes.byref(b), ctypes.byref(g)))
+    return s.value, b.value, g.value
+
+
+def glm_batch_destroy(bt):
+    _check(load().glm_batch_destroy(bt))
+
+
+class Batch:
+    """Owns a batch of independent fits.  problems: list of dicts with keys
+    A (host numpy (m, n) float32), y, loss, lam, eta, iters, seed, b and
+    optionally s (0 = autotuned) and gram ('f32', 'tf32', 'bf16', 'f16')."""
+
+    def __init__(self, problems, dtype="bf16", stream=None):
+        import numpy as np
+        import torch
+        self._keep = []
+        descs = []
+        for pr in problems:
+            A = np.ascontiguousarray(pr["A"], dtype=np.float32)
+            y = np.ascontiguousarray(pr["y"], dtype=np.float32)
+            self._keep += [A, y]
+            d = glm_problem_desc()
+            d.A, d.y = A.ctypes.data, y.ctypes.data
+            d.m, d.n = A.shape
+            d.loss = pr["loss"]
+            d.lambda_, d.eta = pr["lam"], pr["eta"]
+            d.iters, d.seed = pr["iters"], pr["seed"]
+            d.s, d.b = pr.get("s", 0), pr["b"]
+            g = pr.get("gram")
+            d.gram_dtype = -1 if g is None else DTYPES[g]
+            descs.append(d)
+        o = glm_batch_opts_default_struct()
+        o.dtype = DTYPES[dtype]
+        o.input_on_host = 1
+        st = stream if stream is not None else torch.cuda.current_stream()
+        o.stream = st.cuda_stream or 1
+        self.stream = st
+        self.P = len(descs)
+        self.h = glm_batch_create(self.P, descs, o)
+        self._keep = None
+
+    def run(self, xs):
+        return glm_batch_run(self.h, xs)
+
+    def loss(self, xs):
+        return glm_batch_loss(self.h, xs)
+
+    def choice(self, p):
+        return glm_batch_choice(self.h, p)
+
+    def close(self):
+        if getattr(self, "h", None):
+            glm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
