@@ -256,7 +256,7 @@ typedef struct {
   float lambda, eta;
   int64_t iters;     /* SGD-equivalent iterations (0: the problem is idle) */
   uint64_t seed;
-  int s;             /* 1..64, or 0: chosen by the autotuner (4, 8 or 16)  */
+  int s;             /* 1..64, or 0: chosen by the autotuner (1..16)       */
   int64_t b;         /* mini-batch size, 1..1024, s*b <= 8192 (required:
                         b is part of the problem, the tuner never picks it) */
   int gram_dtype;    /* -1: the storage type; else GLM_F32, GLM_TF32,
@@ -277,7 +277,7 @@ void glm_batch_opts_default(glm_batch_opts *o);
 /*
  * Upload P independent problems (each converted like glm_create_ex, with
  * per-column scales) and run the autotuner for every problem with s = 0: for
- * each n among them it times one round of s in {4, 8, 16} on up to 32 of those
+ * each n among them it times one round of s in {1, 2, 4, 8, 16} on up to 32 of those
  * problems (scratch iterates) and keeps the fastest in samples per second.
  * The tuner only chooses what leaves the exact-arithmetic iterate unchanged
  * (s; CA-SGD equals SGD for every s), never b or the operand precision.

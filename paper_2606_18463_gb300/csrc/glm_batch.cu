@@ -17,7 +17,7 @@
 // -- the s-step length (CA-SGD equals SGD for every s) and the Gram kernel --
 // and never the mini-batch b (part of the problem) or the operand precision
 // (which would trade accuracy silently).  For every n among the problems left
-// to it, it times one round of each candidate s in {4, 8, 16} on up to 32 of
+// to it, it times one round of each candidate s in {1, 2, 4, 8, 16} on up to 32 of
 // those problems (scratch iterates) and keeps the fastest in samples/s.
 #include <math.h>
 #include <string.h>
@@ -32,7 +32,7 @@
 namespace glm {
 namespace {
 
-constexpr int64_t kRoundBudget = 512ll << 20;  // bytes of round buffers
+constexpr int64_t kRoundBudget = 4ll << 30;    // bytes of round buffers (HBM is plentiful)
 constexpr int kMaxBatchN = 16384;              // iterate slice in shared memory
 
 bool dev_ptr(const void *p) {
@@ -310,7 +310,7 @@ int autotune(Batch &B) {
                          kv.second.begin() + std::min<size_t>(kv.second.size(), 32));
     int best = 8;
     double best_rate = -1.0;
-    for (int s : {4, 8, 16}) {
+    for (int s : {1, 2, 4, 8, 16}) {
       if (cudaMemsetAsync(xs, 0, xcount * 4, B.stream) != cudaSuccess) {
         rc = set_error(GLM_ECUDA, "autotune: cudaMemsetAsync");
         break;
