@@ -1,7 +1,7 @@
 """Benchmark: CA-SGD samples/s on one GB300 (and N independent replicas).
 
 Workload (default): binary logistic regression, dense A 1,048,576 x 512 FP32
-with entries N(0, 1/512), planted w*, 5% label flips; CA-SGD with s = 16,
+with entries N(0, 1/512), planted w*, 5% label flips; CA-SGD with s = 8,
 b = 64, eta = 0.5, lambda = 0, 65,536 SGD-equivalent iterations; Gram, margin
 and gradient operands in BF16 with FP32 accumulation, FP32 recurrence and
 master weights.  One bench step = one full training run (x reset to 0, then
@@ -9,7 +9,9 @@ master weights.  One bench step = one full training run (x reset to 0, then
 
 Printed: one JSON line (rank 0) with the whole-job samples/s, the
 end-to-end number through the public API with host buffers, the roofline of
-the dominant kernel, the FP32 plain-SGD GPU baseline and the CPU oracle.
+the dominant kernel, the FP32 plain-SGD GPU baseline, the CPU oracle and, as
+an extra object, the batched workload (256 independent logistic / least-
+squares fits of uneven m, n and lambda, BF16 storage, autotuned s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU: one process per GPU (torchrun); each rank runs an independent
@@ -46,6 +48,7 @@ def _args():
     ap.add_argument("--s", type=int, default=8)
     ap.add_argument("--gram", default="bf16", choices=["f32", "tf32", "bf16", "f16"])
     ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip SGD baseline, time-to-target, e2e and CPU legs")
     return ap.parse_args()
@@ -385,10 +388,68 @@ def main():
             out["time_to_target"].update({"target_loss": target, "oracle_loss": f_or,
                                           "oracle_iters": Ts})
     ds.close()
+    if not args.no_extras and not args.no_batch:
+        out["batched"] = _batched(args, torch, synth, glm, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+BATCH = {"P": 256, "b": 64, "iters": 4096, "eta": 0.25, "data_seed": 0}
+
+
+def _batched(args, torch, synth, glm, rank):
+    """The batched workload: 256 independent fits in one run (gather, grouped
+    Gram and a persistent work-queue chain per round; all rounds one CUDA
+    graph); m log-uniform in [4096, 131072], n cycling 64..1024, lambda on
+    10^(-6 + 5 p / 255), even p logistic, odd p least squares; BF16 storage
+    with per-column scales; s chosen by the library's autotuner."""
+    cfg = dict(BATCH)
+    probs = []
+    for sp in synth.batch_specs(P=cfg["P"], seed=cfg["data_seed"]):
+        pr = synth.batch_problem(sp, seed=cfg["data_seed"])
+        probs.append(dict(A=pr.A, y=pr.y, loss=sp["loss"], lam=sp["lam"], eta=cfg["eta"],
+                          iters=cfg["iters"], seed=1000 * (rank + 1) + sp["p"], b=cfg["b"],
+                          s=0))
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    bt = glm.Batch(probs, dtype="bf16", stream=stream)
+    t_create = time.perf_counter() - t0
+    xs = [torch.zeros(p["A"].shape[1], dtype=torch.float32, device="cuda") for p in probs]
+    samples = cfg["P"] * cfg["iters"] * cfg["b"]
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            for x in xs:
+                x.zero_()
+            bt.run(xs)
+        times = []
+        for _ in range(max(args.steps, 1)):
+            for x in xs:
+                x.zero_()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            status = bt.run(xs)
+            e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    choice = {}
+    for p, pr in enumerate(probs):
+        n = int(pr["A"].shape[1])
+        choice.setdefault(str(n), {})
+        sp = str(bt.choice(p)[0])
+        choice[str(n)][sp] = choice[str(n)].get(sp, 0) + 1
+    losses = bt.loss(xs)
+    bt.close()
+    return {"value": samples / (ms / 1e3), "unit": "samples/s", "ms_per_run": ms,
+            "problems": cfg["P"], "rows_total": int(sum(p["A"].shape[0] for p in probs)),
+            "iters_per_problem": cfg["iters"], "b": cfg["b"], "storage": "bf16",
+            "autotuned_s_by_n": choice, "create_and_tune_s": t_create,
+            "nonfinite": int(sum(1 for s_ in status if s_)),
+            "median_final_loss": float(statistics.median(losses))}
 
 
 def _ttt(ds, pr, w, s, b, seed, target, horizon, opts, stream, torch, glm):
