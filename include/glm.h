@@ -23,8 +23,9 @@
  * length s, step size eta, ridge weight lambda, alpha = eta / b,
  * c = 1 - eta * lambda.  The objective is
  *     F(x) = m^-1 sum_i L(a_i^T x, y_i) + (lambda/2) ||x||^2
- * with L the logistic loss log(1 + exp(-y r)) or the squared loss
- * (r - y)^2 / 2 (paper Sec. 2.1; the ridge term is this library's addition).
+ * with L the logistic loss log(1 + exp(-y r)), the squared loss (r - y)^2 / 2
+ * or the Poisson loss e^r - y r (its constant log y! dropped) (paper Sec. 2.1;
+ * the ridge term is this library's addition).
  */
 #ifndef GLM_H_
 #define GLM_H_
@@ -48,6 +49,7 @@ extern "C" {
 /* ---- losses (paper Sec. 2.1) -------------------------------------------- */
 #define GLM_LOGISTIC 0      /* labels must be -1 or +1 */
 #define GLM_LSQ 1           /* least squares / ridge   */
+#define GLM_POISSON 2       /* Poisson counts y >= 0, log link (Sec. 2.1 lists the GLM family) */
 
 /* ---- element types (paper Table 1 storage slots u_A, u_G, u_r, u_g) ------ */
 #define GLM_F32 0

@@ -467,7 +467,8 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
   if (!A || !y) return set_error(GLM_EINVAL, "A or y is NULL");
   if (m < 1 || m >= (1ll << 31)) return set_error(GLM_EINVAL, "m must be in [1, 2^31)");
   if (n < 1 || n > 65536) return set_error(GLM_EINVAL, "n must be in [1, 65536]");
-  if (loss != GLM_LOGISTIC && loss != GLM_LSQ) return set_error(GLM_EINVAL, "unknown loss");
+  if (loss != GLM_LOGISTIC && loss != GLM_LSQ && loss != GLM_POISSON)
+    return set_error(GLM_EINVAL, "unknown loss");
   if (dtype != GLM_F32 && dtype != GLM_BF16 && dtype != GLM_F16)
     return set_error(GLM_EINVAL, "storage dtype must be GLM_F32, GLM_BF16 or GLM_F16");
   glm_create_opts d;
@@ -568,7 +569,9 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
   if (flag & FLAG_BAD_LABEL)
     return fail(set_error(GLM_EINVAL, loss == GLM_LOGISTIC
                                           ? "logistic labels must be exactly -1 or +1"
-                                          : "labels must be finite"));
+                                          : loss == GLM_POISSON
+                                                ? "Poisson labels must be finite and >= 0"
+                                                : "labels must be finite"));
 #undef CK
   *out = reinterpret_cast<glm_handle>(h);
   return GLM_OK;

@@ -389,7 +389,8 @@ int glm_batch_create(int P, const glm_problem_desc *descs, const glm_batch_opts 
     if (d.b < 1 || d.b > 1024) return set_error(GLM_EINVAL, "batched b must be in [1, 1024]");
     if (d.s < 0 || d.s > 64) return set_error(GLM_EINVAL, "s must be 0 (autotuned) or in [1, 64]");
     if (d.iters < 0) return set_error(GLM_EINVAL, "iters must be >= 0");
-    if (d.loss != GLM_LOGISTIC && d.loss != GLM_LSQ) return set_error(GLM_EINVAL, "bad loss");
+    if (d.loss != GLM_LOGISTIC && d.loss != GLM_LSQ && d.loss != GLM_POISSON)
+      return set_error(GLM_EINVAL, "bad loss");
     if (!(d.eta > 0.f) || !isfinite(d.eta)) return set_error(GLM_EINVAL, "eta must be > 0");
     if (!(d.lambda >= 0.f) || !isfinite(d.lambda)) return set_error(GLM_EINVAL, "lambda must be >= 0");
     const double c = 1.0 - (double)d.eta * (double)d.lambda;

@@ -348,6 +348,7 @@ template <> __device__ __forceinline__ float dloss<float>(int loss, float z, flo
     const float sig_neg_t = (t >= 0.f) ? e * inv : inv;
     return -y * sig_neg_t;
   }
+  if (loss == GLM_POISSON) return expf(z) - y;
   return z - y;
 }
 
@@ -358,6 +359,7 @@ template <> __device__ __forceinline__ double dloss<double>(int loss, double z, 
     const double sig_neg_t = (t >= 0.0) ? e / (1.0 + e) : 1.0 / (1.0 + e);
     return -y * sig_neg_t;
   }
+  if (loss == GLM_POISSON) return exp(z) - y;
   return z - y;
 }
 
@@ -366,6 +368,7 @@ __device__ __forceinline__ float loss_term(int loss, float z, float y) {
     const float t = y * z;
     return fmaxf(-t, 0.f) + log1pf(expf(-fabsf(t)));
   }
+  if (loss == GLM_POISSON) return expf(z) - y * z;
   const float d = z - y;
   return 0.5f * d * d;
 }

@@ -168,7 +168,8 @@ __global__ void k_check_labels(const float *y, int64_t m, int loss, unsigned *fl
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float v = y[i];
-    if (!isfinite(v) || (loss == GLM_LOGISTIC && v != 1.f && v != -1.f))
+    if (!isfinite(v) || (loss == GLM_LOGISTIC && v != 1.f && v != -1.f) ||
+        (loss == GLM_POISSON && v < 0.f))
       atomicOr(flag, FLAG_BAD_LABEL);
   }
 }

@@ -24,7 +24,7 @@ GLM_OK, GLM_EINVAL, GLM_ENOMEM, GLM_ECUDA, GLM_ENONFINITE, GLM_ETIMEOUT, GLM_EUN
 STATUS_NAMES = {0: "GLM_OK", 1: "GLM_EINVAL", 2: "GLM_ENOMEM", 3: "GLM_ECUDA",
                 4: "GLM_ENONFINITE", 5: "GLM_ETIMEOUT", 6: "GLM_EUNSUPPORTED"}
 # losses
-GLM_LOGISTIC, GLM_LSQ = 0, 1
+GLM_LOGISTIC, GLM_LSQ, GLM_POISSON = 0, 1, 2
 # element types
 GLM_F32, GLM_BF16, GLM_F16, GLM_TF32, GLM_E4M3, GLM_F64 = range(6)
 DTYPES = {"f32": GLM_F32, "bf16": GLM_BF16, "f16": GLM_F16, "tf32": GLM_TF32,

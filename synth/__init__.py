@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-LOGISTIC, LSQ = 0, 1
+LOGISTIC, LSQ, POISSON = 0, 1, 2
 
 
 @dataclass
@@ -110,6 +110,20 @@ def lsq_planted(m: int, n: int, seed: int = 0, noise: float = 0.1,
         y[i:i + blk.shape[0]] = blk + noise * rng.standard_normal(blk.shape[0])
     return Problem(A, y, LSQ, lam, {"recipe": "lsq_planted", "seed": seed,
                                      "noise": noise, "x_star": xs})
+
+
+def poisson_planted(m: int, n: int, seed: int = 0, scale: float = 0.5,
+                    lam: float = 0.0) -> Problem:
+    """Poisson regression with the log link: A_ij ~ N(0, 1/n), x*_j ~ N(0, scale^2),
+    y_i ~ Poisson(exp(a_i^T x*)) as float32 counts (margins are O(scale))."""
+    rng = np.random.default_rng([seed, 404, m, n])
+    A = _normal_f32(rng, (m, n), 1.0 / math.sqrt(n))
+    w = rng.normal(0.0, scale, n)
+    r = np.zeros(m)
+    for i in range(0, m, 1 << 16):
+        r[i:i + (1 << 16)] = A[i:i + (1 << 16)].astype(np.float64) @ w
+    y = rng.poisson(np.exp(r)).astype(np.float32)
+    return Problem(A=A, y=y, loss=POISSON, lam=lam, meta={"w_star": w})
 
 
 def to_bf16_values(A: np.ndarray) -> np.ndarray:

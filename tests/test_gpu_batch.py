@@ -27,7 +27,8 @@ def G():
 # last outer steps (200 iterations)
 SPECS = [(700, 64, oracle.LOGISTIC, 1e-3, 4), (1500, 100, oracle.LSQ, 1e-2, 8),
          (3000, 256, oracle.LOGISTIC, 1e-4, 3), (900, 64, oracle.LSQ, 0.0, 1),
-         (2500, 130, oracle.LOGISTIC, 0.0, 16), (400, 33, oracle.LSQ, 1e-3, 5)]
+         (2500, 130, oracle.LOGISTIC, 0.0, 16), (400, 33, oracle.LSQ, 1e-3, 5),
+         (2000, 72, oracle.POISSON, 1e-3, 4)]
 ITERS, B, ETA = 200, 16, 0.25
 
 
@@ -36,6 +37,8 @@ def _make(specs, seed0=0):
     for k, (m, n, loss, lam, s) in enumerate(specs):
         if loss == oracle.LOGISTIC:
             pr = synth.logistic_planted(m, n, seed=seed0 + k, lam=lam)
+        elif loss == oracle.POISSON:
+            pr = synth.poisson_planted(m, n, seed=seed0 + k, lam=lam)
         else:
             pr = synth.lsq_planted(m, n, seed=seed0 + k, noise=0.1, lam=lam)
         out.append(dict(A=pr.A, y=pr.y, loss=loss, lam=lam, eta=ETA, iters=ITERS,

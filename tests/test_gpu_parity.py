@@ -298,3 +298,36 @@ def test_nonfinite_detected(G):
     ds.ca_sgd(x, 4, 8, 0.9, 0.0, 4000, 0, gram_dtype="f32")  # diverges
     assert G.glm_sync(ds.h) == G.GLM_ENONFINITE
     assert G.glm_sync(ds.h) == G.GLM_OK  # flag cleared
+
+
+# ----------------------------------------------------------------------------
+# Poisson loss (log link): u = e^z - y, L = e^z - y z
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("s,C", [(1, 4), (4, 1), (8, 8), (8, 16), (5, 2)])
+def test_poisson_parity(G, s, C):
+    pr = synth.poisson_planted(4000, 96, seed=5, lam=1e-3)
+    ds = _ds(G, pr)
+    x = _run(G, ds, pr, s, 16, 0.05, 1e-3, 1000, 3, sgd=(s == 1), cluster=C,
+             **({} if s == 1 else {"gram_dtype": "f32"}))
+    ref = oracle.sgd(pr.A, pr.y, pr.loss, 16, 0.05, 1e-3, 1000, 3)
+    assert _rel(x, ref) <= 1e-5, _rel(x, ref)
+
+
+def test_poisson_loss_storage_and_labels(G):
+    pr = synth.poisson_planted(6000, 128, seed=6, lam=1e-3)
+    ds = _ds(G, pr)
+    x = _run(G, ds, pr, 8, 32, 0.05, 1e-3, 2000, 1, gram_dtype="f32")
+    f_gpu = ds.loss_value(torch.tensor(x, dtype=torch.float32, device="cuda"), 1e-3)
+    f_or = oracle.loss(pr.A, pr.y, pr.loss, 1e-3, x.astype(np.float32).astype(np.float64))
+    assert abs(f_gpu - f_or) <= 1e-6 * abs(f_or)
+    dsb = _ds(G, pr, "bf16")
+    xb = _run(G, dsb, pr, 8, 32, 0.05, 1e-3, 2000, 1, gram_dtype="bf16")
+    ref = oracle.sgd(pr.A, pr.y, pr.loss, 32, 0.05, 1e-3, 2000, 1)
+    fb = oracle.loss(pr.A, pr.y, pr.loss, 1e-3, xb)
+    fr = oracle.loss(pr.A, pr.y, pr.loss, 1e-3, ref)
+    assert abs(fb - fr) <= 1e-3 * abs(fr)
+    bad = pr.y.copy()
+    bad[7] = -1.0
+    with pytest.raises(G.GlmError) as e:
+        G.Dataset(torch.from_numpy(pr.A).cuda(), torch.from_numpy(bad).cuda(), G.GLM_POISSON)
+    assert e.value.code == G.GLM_EINVAL

@@ -25,6 +25,8 @@ def _tiny(m=8, n=3, seed=0, loss=LSQ):
     A = (rng.standard_normal((m, n)) / np.sqrt(n)).astype(np.float32)
     if loss == LSQ:
         y = rng.standard_normal(m).astype(np.float32)
+    elif loss == oracle.POISSON:
+        y = rng.poisson(1.0, m).astype(np.float32)
     else:
         y = np.where(rng.random(m) < 0.5, -1.0, 1.0).astype(np.float32)
     return A, y
@@ -96,7 +98,7 @@ def test_ca_sgd_s2_hand_expanded():
 # ----------------------------------------------------------------------------
 # Exact-arithmetic identity: CA-SGD(s) == SGD (Assumption 6 / Sec. 2.2)
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("loss", [LOG, LSQ])
+@pytest.mark.parametrize("loss", [LOG, LSQ, oracle.POISSON])
 @pytest.mark.parametrize("s", [1, 2, 3, 4, 7, 8, 16, 32, 64])
 def test_ca_equals_sgd(loss, s):
     A, y = _tiny(64, 5, seed=s, loss=loss)
@@ -184,6 +186,21 @@ def test_risk_closed_forms():
         tot += math.log(1.0 + math.exp(-t))
     ref = tot / 16 + 0.5 * lam * float(x @ x)
     assert abs(oracle.loss(A, y, LOG, lam, x) - ref) < 1e-13
+
+
+def test_poisson_risk_closed_form_and_brute_force():
+    # F(0) = mean(e^0 - y 0) = 1 exactly; at a nonzero point, a brute-force sum
+    import math
+    A, y = _tiny(16, 4, seed=5, loss=oracle.POISSON)
+    assert oracle.loss(A, y, oracle.POISSON, 0.0, np.zeros(4)) == 1.0
+    x = np.array([0.3, -0.7, 0.1, 1.2])
+    lam = 0.2
+    tot = 0.0
+    for i in range(16):
+        r = sum(float(A[i, k]) * x[k] for k in range(4))
+        tot += math.exp(r) - float(y[i]) * r
+    ref = tot / 16 + 0.5 * lam * float(x @ x)
+    assert abs(oracle.loss(A, y, oracle.POISSON, lam, x) - ref) < 1e-13
 
 
 def test_gram_lower_brute_force():
