@@ -14,17 +14,21 @@
 //    and residuals, then sends c^{-j} u_j to every CTA.
 //
 // Warp roles in each CTA: 16 consumer warps do the arithmetic above and
-// synchronise among themselves only (named barrier 1); one producer warp
+// synchronise among themselves only (named barrier 1).  During the
+// recurrence, up to four row warps (warps 0 mod 4) each own groups of four
+// rows and run the serial loop, while the twelve other consumer warps fold
+// each block's Y_j^T u_j into the update as soon as it lands.  One producer warp
 // streams everything x-independent into shared memory ahead of use -- the
 // CTA's column slice of the rows of Y and their labels (TMA 2D tiles and a
 // bulk copy, `ns` outer steps in flight) and the own rows of G_{j,<j} (bulk
 // copies; a whole outer step ahead when two steps fit, else one block row
 // ahead) -- gated by full / empty mbarriers.  x-dependent values travel one
 // way: (vector) st.async into the owner's shared memory, completing
-// transaction bytes on the owner's mbarrier, so an inner step costs one
-// DSMEM latency and no cluster barrier.  Every wait is bounded
-// (FLAG_TIMEOUT; the kernel then drains its own copies and unwinds without
-// writing x).  Slices that do not fit are read from global memory directly.
+// transaction bytes on the owner's mbarrier (one per block of residuals), so
+// an inner step costs one DSMEM latency and no cluster or CTA barrier.
+// Every wait is bounded (FLAG_TIMEOUT; the kernel then drains its own copies
+// and unwinds without writing x).  Slices that do not fit are read from
+// global memory directly.
 //
 // The c^{-i} scaling of the stored residual history turns the per-block
 // weights c^{j-1-i} of the ridge-decayed recurrence into one scalar per row
@@ -41,6 +45,7 @@ namespace {
 constexpr int kCThreads = 512;              // consumer threads (warps 0..15)
 constexpr int kCWarps = kCThreads / 32;
 constexpr int kThreads = kCThreads + 32;    // + one producer warp
+constexpr int kWThreads = kCThreads - kCWarps / 4 * 32;  // update workers: warps w % 4 != 0
 constexpr long long kWaitBudget = 4000000000ll;  // SM cycles (~2 s)
 constexpr size_t kSmemMax = 227 * 1024 - 2048;  // leave room for static shared memory
 constexpr int kMaxSlots = 4;
@@ -79,7 +84,7 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t b, int s, int C
   L.off_rown = take((size_t)s * L.rpb * tr_bytes, 16);
   L.off_yown = take((size_t)s * L.rpb * 4, 16);
   L.off_part = take((size_t)kCThreads * 8 * 4, 16);
-  L.off_bar = take(16 * 8, 16);
+  L.off_bar = take((size_t)(16 + s) * 8, 16);  // 15 pipeline barriers, one per block
   L.off_coef = take((size_t)3 * (s + 1) * tr_bytes, 16);  // c^j, c^-j, alpha c^(j-1)
   L.off_rem = take((size_t)4 * 16 * 4, 16);                 // mapa'd remote addresses
   const size_t base = off;
@@ -169,31 +174,117 @@ template <> struct Raw8<__half> {
 
 constexpr int kRows = 4;  // consecutive rows per thread group in the margin
 
-// Lane-strided dot product of one G row with the residual history over
-// [0, jb), four independent partial sums in a fixed order.  Instantiated once
-// for staged rows (shared memory) and once for rows read from global memory,
-// so each instance uses a single address space.
+// Four consecutive entries of the residual history.
+__device__ __forceinline__ void load4(const float *p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&o)[4]) {
+  const double2 v0 = reinterpret_cast<const double2 *>(p)[0];
+  const double2 v1 = reinterpret_cast<const double2 *>(p)[1];
+  o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+
+// Per-lane partial correction dot products of up to four G rows (row i at
+// grow + i * rs, 16-byte aligned) with the residual history over [0, jb):
+// lane-strided 4-element chunks, then a scalar tail when jb % 4 != 0.  One
+// running sum per row, in a fixed order.  Rows past nq re-read the last
+// valid row, so every load is in bounds and unconditional and a chunk's five
+// loads are in flight together; only their FMAs are skipped (the caller
+// discards those sums).
+// Instantiated once for staged rows (shared memory) and once for global.
 template <typename TR, bool kShared>
-__device__ __forceinline__ TR row_dot(const float *__restrict__ grow,
-                                      const TR *__restrict__ uh, int jb, int lane) {
-  TR a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int c = lane;
+__device__ __forceinline__ void rows_dot4(const float *__restrict__ grow, int64_t rs, int nq,
+                                          const TR *__restrict__ uh, int jb, int lane,
+                                          TR (&acc)[4]) {
+  const float *rp[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) rp[i] = grow + (i < nq ? i : nq - 1) * rs;
+  const int jb4 = jb & ~3;
 #pragma unroll 2
-  for (; c + 96 < jb; c += 128) {
-    float g0, g1, g2, g3;
-    if (kShared) {
-      g0 = grow[c]; g1 = grow[c + 32]; g2 = grow[c + 64]; g3 = grow[c + 96];
-    } else {
-      g0 = __ldg(grow + c); g1 = __ldg(grow + c + 32);
-      g2 = __ldg(grow + c + 64); g3 = __ldg(grow + c + 96);
+  for (int c = 4 * lane; c < jb4; c += 128) {
+    TR u[4];
+    load4(uh + c, u);
+    float4 g[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 *p = reinterpret_cast<const float4 *>(rp[i] + c);
+      g[i] = kShared ? *p : __ldg(p);
     }
-    a0 += (TR)g0 * uh[c];
-    a1 += (TR)g1 * uh[c + 32];
-    a2 += (TR)g2 * uh[c + 64];
-    a3 += (TR)g3 * uh[c + 96];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i < nq) {
+        acc[i] = fma((TR)g[i].x, u[0], acc[i]);
+        acc[i] = fma((TR)g[i].y, u[1], acc[i]);
+        acc[i] = fma((TR)g[i].z, u[2], acc[i]);
+        acc[i] = fma((TR)g[i].w, u[3], acc[i]);
+      }
+    }
   }
-  for (; c < jb; c += 32) a0 += (TR)(kShared ? grow[c] : __ldg(grow + c)) * uh[c];
+  const int c = jb4 + lane;
+  if (c < jb) {
+    const TR uc = uh[c];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < nq) acc[i] = fma((TR)(kShared ? rp[i][c] : __ldg(rp[i] + c)), uc, acc[i]);
+  }
+}
+
+// Per-lane partial correction dot product of one G row with the residual
+// history over [0, jb) in the recurrence type (FP64): lane-strided 4-element
+// chunks into four running sums (independent FMA chains), combined pairwise.
+template <typename TR, bool kShared>
+__device__ __forceinline__ TR row_dot1(const float *__restrict__ grow, const TR *__restrict__ uh,
+                                       int jb, int lane) {
+  TR a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  const int jb4 = jb & ~3;
+  for (int c = 4 * lane; c < jb4; c += 128) {
+    TR u[4];
+    load4(uh + c, u);
+    const float4 *p = reinterpret_cast<const float4 *>(grow + c);
+    const float4 g = kShared ? *p : __ldg(p);
+    a0 = fma((TR)g.x, u[0], a0);
+    a1 = fma((TR)g.y, u[1], a1);
+    a2 = fma((TR)g.z, u[2], a2);
+    a3 = fma((TR)g.w, u[3], a3);
+  }
+  const int c = jb4 + lane;
+  if (c < jb) a0 = fma((TR)(kShared ? grow[c] : __ldg(grow + c)), uh[c], a0);
   return (a0 + a1) + (a2 + a3);
+}
+
+// Warp totals of four per-lane values, transposed: on return lane L holds the
+// total of value L >> 3.  Lanes first split the four values between the two
+// half-warps (xor 16), then between quarter-warps (xor 8), then finish each
+// value within its group of eight lanes: six shuffles, fixed order.
+template <typename TR>
+__device__ __forceinline__ TR warp_sum4_t(const TR (&v)[4], int lane) {
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  const TR w0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, h16 ? v[0] : v[2], 16);
+  const TR w1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, h16 ? v[1] : v[3], 16);
+  TR x = (h8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, h8 ? w0 : w1, 8);
+  x += __shfl_xor_sync(0xffffffffu, x, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  return x;
+}
+
+// Four residuals into one 16-byte-aligned remote slot.
+__device__ __forceinline__ void send4(uint32_t ra, const float (&w)[4], uint32_t rb) {
+  st_async_v4(ra, w[0], w[1], w[2], w[3], rb);
+}
+
+// Bounded wait that also gives up once another thread of the CTA has flagged
+// an abort; `nap` lets waiters off the critical path yield issue slots.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
+                                              const volatile int *abort_flag, bool nap) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test_wait(bar, parity)) {
+    if (*abort_flag || clock64() - t0 > kWaitBudget) return false;
+    if (nap) __nanosleep(32);
+  }
+  return true;
 }
 
 __device__ __forceinline__ void csync() { named_sync(1, kCThreads); }
@@ -213,6 +304,17 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const int64_t col0 = (int64_t)rank * nc;
   const int64_t l0 = (int64_t)rank * rpb;
   const int nown = (int)max((int64_t)0, min((int64_t)rpb, b - l0));
+  // Recurrence row warps, each taking its own rows four at a time.  FP32:
+  // warps 0, 4, 8, 12 (one SM sub-partition, which no worker warp shares)
+  // with contiguous groups, so a group's residuals leave as one 16-byte store.
+  // FP64: rows dealt round-robin to warps 0, 1, 2, ... so that the FP64
+  // work spreads over every sub-partition (the FP64 pipe is the bound
+  // there): up to four row warps, leaving warps 4..15 to the update, or,
+  // with more than four own rows, every consumer warp (the update then
+  // follows the recurrence).
+  constexpr bool kF64 = sizeof(TR) == 8;
+  const bool all_rows = kF64 && nown > 4;
+  const int nrw = kF64 ? min(nown, kCWarps) : min((nown + 3) / 4, 4);
 
   extern __shared__ __align__(1024) unsigned char smem[];
   float *xs = reinterpret_cast<float *>(smem);
@@ -232,12 +334,14 @@ k_chain(const __grid_constant__ ChainArgs a) {
 
   const uint32_t bar0 = smem_u32(smem + L.off_bar);
   const uint32_t bar_r = bar0;                       // margin partials
-  const uint32_t bar_u0 = bar0 + 8;                  // residuals (x2)
+  const uint32_t bar_u = bar0 + 8 * 16;              // residuals of block j: + 8 j
   const uint32_t full_g0 = bar0 + 24, empty_g0 = bar0 + 40;   // x2 each
   const uint32_t full_y0 = bar0 + 56, empty_y0 = bar0 + 88;   // x kMaxSlots each
 
   if (tid == 0) {
-    for (int i = 0; i < 15; ++i) mbar_init(bar0 + 8 * i, 1);
+    for (int i = 0; i < 15; ++i)  // G_BLOCK: every row warp releases a G slot
+      mbar_init(bar0 + 8 * i, (gmode == G_BLOCK && i >= 5 && i < 7) ? nrw : 1);
+    for (int j = 0; j < s; ++j) mbar_init(bar_u + 8 * j, 1);
     fence_mbar_init_cluster();
     s_abort = 0;
   }
@@ -250,7 +354,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
     rem[tid] = mapa(smem_u32(rrecv), tid);
     rem[16 + tid] = mapa(bar_r, tid);
     rem[32 + tid] = mapa(smem_u32(uh), tid);
-    rem[48 + tid] = mapa(bar_u0, tid);
+    rem[48 + tid] = mapa(bar_u, tid);
   }
   for (int c = tid; c < nc; c += kThreads) xs[c] = (col0 + c < n) ? a.x[col0 + c] : 0.f;
   const int64_t gsz = gram_size(s, b);
@@ -311,8 +415,10 @@ k_chain(const __grid_constant__ ChainArgs a) {
           bool stop = false;
           for (int j = 1; j < shh; ++j, ++kblk) {
             const int slot = (int)(kblk & 1);
-            if (kblk >= 2 && !mbar_wait_sleep(empty_g0 + 8 * slot,
-                                                (uint32_t)(((kblk >> 1) - 1) & 1), kWaitBudget)) {
+            // a refill is one block ahead of the recurrence: spin (with short
+            // naps) rather than let the hardware suspend this thread
+            if (kblk >= 2 && !wait_or_abort(empty_g0 + 8 * slot,
+                                            (uint32_t)(((kblk >> 1) - 1) & 1), vabort, true)) {
               atomicOr(&s_abort, 1);
               stop = true;
               break;
@@ -356,7 +462,6 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const int loss_kind = a.loss;
   unsigned *const flag = a.flag;
   const TY *Y = static_cast<const TY *>(a.Y);
-  uint32_t J = 0;         // inner steps completed in this launch
   int64_t kblk = 0;       // G block rows consumed (G_BLOCK mode)
   bool abort = false;
 
@@ -366,6 +471,9 @@ k_chain(const __grid_constant__ ChainArgs a) {
     const int64_t row0 = (int64_t)h * sb;
     const float *Gh = a.G + (int64_t)h * gsz;
     if (tid == 0) mbar_arrive_expect_tx(bar_r, (uint32_t)(C * sh * nown * 4));
+    if (warp == 0)  // every block's residuals: b values from the whole cluster
+      for (int j = lane; j < sh; j += 32)
+        mbar_arrive_expect_tx(bar_u + 8 * j, (uint32_t)(b * sizeof(TR)));
     const bool staged = ns > 0;
     const TY *Ys;          // row r of this CTA's slice at Ys + r * ystride
     int64_t ystride;
@@ -480,149 +588,288 @@ k_chain(const __grid_constant__ ChainArgs a) {
     csync();
     if (s_abort) { abort = true; break; }
 
-    // ---- D: inner s-step recurrence (row warps only) ------------------------
-    // Only the warps that own rows run the serial loop and synchronise on
-    // named barrier 2; the other consumer warps park at the barrier below for
-    // the whole recurrence, so they take no issue slots from the critical path.
-    const int nrw = nown < kCWarps ? nown : kCWarps;
-    if (warp < nrw) {
-      int64_t goff = 0;   // floats into the G_STEP slot
-      for (int j = 0; j < sh; ++j) {
-        const int64_t ldj = gram_ld(j, b);
-        int64_t gofs = 0;  // float offset of this block row's own rows
-        if (j > 0) {
-          if (gmode == G_STEP) {
-            gofs = (h & 1) * L.gslot_floats + goff;
-            goff += (int64_t)rpb * ldj;
-          } else if (gmode == G_BLOCK) {
-            if (tid == 0 && !mbar_wait_bounded(full_g0 + 8 * (kblk & 1),
-                                               (uint32_t)((kblk >> 1) & 1), kWaitBudget))
-              atomicOr(&s_abort, 1);
-            named_sync(2, nrw * 32);
-            gofs = (kblk & 1) * L.gslot_floats;
-          } else {
-            gofs = gram_off(j, b) + l0 * ldj;
-          }
-        }
-        // one warp per own row: correction dot product (4 independent partial
-        // sums, fixed order), shuffle-tree total in every lane, residual, and a
-        // lane-parallel fan-out of c^{-j} u to the C CTAs (one instruction)
-        const int jb = (int)(j * b);
-        const uint32_t ubar = 8 * (J & 1);
-        for (int rr = warp; rr < nown; rr += nrw) {
-          TR corr = 0;
+    // ---- D + E: recurrence on the row warps, update on the worker warps ----
+    // Row warps run the serial loop over blocks.  Block j of every CTA lands on this CTA's barrier bar_u[j]; a row warp
+    // waits on it before block j + 1, and the worker warps (w % 4 != 0) wait
+    // on it before folding Y_j^T (c^{-j} u_j) into their Kahan sums, so the
+    // update runs under the recurrence instead of after it.  Workers: the
+    // twelve consumer warps that are not row-warp candidates.
+    const uint32_t upar = (uint32_t)(h & 1);
+    const volatile int *vab = &s_abort;
+    // update: 0 = folded in block by block by the workers, 1 = after the
+    // recurrence by every consumer thread (row groups), 2 = after the
+    // recurrence, one thread per 8-column vector (slices wider than that)
+    const int emode = (!all_rows && V <= kWThreads) ? 0 : (V <= kCThreads ? 1 : 2);
+    const bool inc_e = emode == 0;
+    const int EG = emode == 0 ? kWThreads / V : (emode == 1 ? kCThreads / V : 1);  // row groups
+    const bool row_warp = kF64 ? warp < nrw : ((warp & 3) == 0 && (warp >> 2) < nrw);
+    const bool worker = kF64 ? (warp >= 4 && !all_rows) : (warp & 3) != 0;
+    if (row_warp) {
+      const int rw = kF64 ? warp : warp >> 2;
+      const uint32_t ra_u = lane < C ? rem[32 + lane] : 0u;  // CTA lane's residual history
+      const uint32_t rb_u = lane < C ? rem[48 + lane] : 0u;  // and its block barriers
+      {
+        int64_t goff = 0;  // floats into the G_STEP slot
+        for (int j = 0; j < sh; ++j) {
+          const int64_t ldj = gram_ld(j, b);
+          int64_t gofs = 0;  // float offset of this block row's own rows
           if (j > 0) {
-            corr = gmode != G_NONE
-                       ? row_dot<TR, true>(gbuf + gofs + rr * ldj, uh, jb, lane)
-                       : row_dot<TR, false>(Gh + gofs + rr * ldj, uh, jb, lane);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) corr += __shfl_xor_sync(0xffffffffu, corr, off);
+            // lane 0 polls (a whole warp of probes would load the shared-memory
+            // pipe the other lanes' reads depend on); the warp then follows
+            int ok = 1;
+            if (lane == 0) {
+              ok = wait_or_abort(bar_u + 8 * (j - 1), upar, vab, false);
+              if (ok && gmode == G_BLOCK)
+                ok = wait_or_abort(full_g0 + 8 * (kblk & 1), (uint32_t)((kblk >> 1) & 1), vab,
+                                   false);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+              if (lane == 0) atomicOr(&s_abort, 1);
+              break;
+            }
+            if (gmode == G_STEP) {
+              gofs = (h & 1) * L.gslot_floats + goff;
+              goff += (int64_t)rpb * ldj;
+            } else if (gmode == G_BLOCK) {
+              gofs = (kblk & 1) * L.gslot_floats;
+            } else {
+              gofs = gram_off(j, b) + l0 * ldj;
+            }
           }
-          const TR z = cpw[j] * rown[j * rpb + rr] - zcw[j] * corr;
-          const TR u = dloss<TR>(loss_kind, z, (TR)yown[j * rpb + rr]);
-          if (lane == 0 && (!isfinite(z) || !isfinite(u))) atomicOr(flag, FLAG_NONFINITE);
-          const TR uw = u * cinw[j];
-          const uint32_t offu = (uint32_t)(((int64_t)j * b + l0 + rr) * sizeof(TR));
-          for (int d = lane; d < C; d += 32) st_async(rem[32 + d] + offu, uw, rem[48 + d] + ubar);
+          const int jb = (int)(j * b);
+          const TR cj = cpw[j], zj = zcw[j], ij = cinw[j];
+          if constexpr (kF64) {  // one row at a time, rows rw, rw + nrw, ...
+            for (int rq = rw; rq < nown; rq += nrw) {
+              const TR rv = rown[j * rpb + rq];
+              const TR yv = (TR)yown[j * rpb + rq];
+              TR corr = 0;
+              if (j > 0) {
+                corr = gmode != G_NONE
+                           ? row_dot1<TR, true>(gbuf + gofs + rq * ldj, uh, jb, lane)
+                           : row_dot1<TR, false>(Gh + gofs + rq * ldj, uh, jb, lane);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                  corr += __shfl_xor_sync(0xffffffffu, corr, off);
+              }
+              const TR z = cj * rv - zj * corr;
+              const TR u = dloss<TR>(loss_kind, z, yv);
+              if (lane == 0 && (!isfinite(z) || !isfinite(u))) atomicOr(flag, FLAG_NONFINITE);
+              if (lane < C)
+                st_async(ra_u + (uint32_t)((jb + l0 + rq) * sizeof(TR)), u * ij, rb_u + 8 * j);
+            }
+          } else {  // FP32: contiguous groups of four rows
+            for (int q0 = 4 * rw; q0 < nown; q0 += 4 * nrw) {
+              // rows q0 + i, i < nq; lane L finishes row L >> 3
+              const int nq = min(4, nown - q0);
+              const int64_t rs = ldj;
+              const int q = lane >> 3;
+              const int rq = q0 + (q < nq ? q : nq - 1);
+              const TR rv = rown[j * rpb + rq];
+              const TR yv = (TR)yown[j * rpb + rq];
+              TR acc[4] = {0, 0, 0, 0};
+              if (j > 0) {
+                if (gmode != G_NONE)
+                  rows_dot4<TR, true>(gbuf + gofs + q0 * ldj, rs, nq, uh, jb, lane, acc);
+                else
+                  rows_dot4<TR, false>(Gh + gofs + q0 * ldj, rs, nq, uh, jb, lane, acc);
+              }
+              const TR corr = warp_sum4_t(acc, lane);
+              const TR z = cj * rv - zj * corr;
+              const TR u = dloss<TR>(loss_kind, z, yv);
+              if (q < nq && (lane & 7) == 0 && (!isfinite(z) || !isfinite(u)))
+                atomicOr(flag, FLAG_NONFINITE);
+              const TR uw = u * ij;
+              TR w[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) w[i] = __shfl_sync(0xffffffffu, uw, 8 * i);
+              if (lane < C) {  // fan-out: lane d writes CTA d's copy of block j
+                const uint32_t ra = ra_u + (uint32_t)((jb + l0 + q0) * sizeof(TR));
+                const uint32_t rb = rb_u + 8 * j;
+                if (vsend_r && nq == 4) {
+                  send4(ra, w, rb);
+                } else {
+#pragma unroll
+                  for (int i = 0; i < 4; ++i)
+                    if (i < nq) st_async(ra + (uint32_t)(i * sizeof(TR)), w[i], rb);
+                }
+              }
+            }
+          }
+          if (gmode == G_BLOCK && j > 0) {  // this warp is done with the G block row
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_g0 + 8 * (kblk & 1));
+            ++kblk;
+          }
         }
-        if (tid == 0) {
-          mbar_arrive_expect_tx(bar_u0 + 8 * (J & 1), (uint32_t)(b * sizeof(TR)));
-          if (!mbar_wait_bounded(bar_u0 + 8 * (J & 1), (J >> 1) & 1, kWaitBudget))
-            atomicOr(&s_abort, 1);
-        }
-        ++J;
-        named_sync(2, nrw * 32);
-        if (gmode == G_BLOCK && j > 0) {  // every row warp is done with this G block row
-          if (tid == 0) mbar_arrive(empty_g0 + 8 * (kblk & 1));
-          ++kblk;
-        }
-        if (s_abort) break;
       }
-    }
-    csync();
-    if (s_abort) { abort = true; break; }
-    if (gmode == G_STEP && sh >= 2 && tid == 0) mbar_arrive(empty_g0 + 8 * (h & 1));
-
-    // ---- E: x <- c^{sh} x - alpha c^{sh-1} Y^T (c^{-j} u), own slice ---------
-    {
-      const int RG = kCThreads / V;
-      const int g = tid / V, v = tid - (tid / V) * V;
-      const int64_t col = (int64_t)v * 8;
+    } else if (worker && inc_e) {
+      const int wt = (kF64 ? warp - 4 : warp - (warp >> 2) - 1) * 32 + lane;  // worker index
+      const int eg = wt / V, ev = wt - (wt / V) * V;
+      const int64_t ecol = (int64_t)ev * 8;
       float acc[8], cmp[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) { acc[i] = 0.f; cmp[i] = 0.f; }
-      if (g < RG && col0 + col < n) {
-        for (int64_t rb = g; rb < R; rb += (int64_t)RG * 4) {
-          Raw8<TY> raw[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int64_t r = rb + (int64_t)u * RG;
-            if (r < R) raw[u].load(Ys + r * ystride + col, staged);
-            else raw[u].zero();
+      // every worker with rows waits on every block (thread 0 always does, so
+      // each phase of bar_u is observed before the next step re-arms it)
+      const bool cols = col0 + ecol < n;
+      // the lanes with rows form a prefix of the warp (groups ascend with the
+      // thread index); the lowest of them polls for all
+      const unsigned act = __ballot_sync(0xffffffffu, eg < EG && eg < b);
+      if (eg < EG && eg < b) {
+        const int leader = __ffs(act) - 1;
+        for (int j = 0; j < sh; ++j) {
+          int ok = 1;
+          if (lane == leader) ok = wait_or_abort(bar_u + 8 * j, upar, vab, true);
+          if (!__shfl_sync(act, ok, leader)) {
+            atomicOr(&s_abort, 1);
+            break;
           }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int64_t r = rb + (int64_t)u * RG;
-            if (r >= R) break;
+          if (!cols) continue;
+          for (int64_t r = (int64_t)j * b + eg; r < (int64_t)(j + 1) * b; r += EG) {
+            Raw8<TY> raw;
+            raw.load(Ys + r * ystride + ecol, staged);
             float f[8];
-            raw[u].get(f);
-            const float w = (float)uh[r];
+            raw.get(f);
+            const float wv = (float)uh[r];
             if (a.kahan) {
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const float yv = fmaf(f[i], w, -cmp[i]);
+                const float yv = fmaf(f[i], wv, -cmp[i]);
                 const float t2 = acc[i] + yv;
                 cmp[i] = (t2 - acc[i]) - yv;
                 acc[i] = t2;
               }
             } else {
 #pragma unroll
-              for (int i = 0; i < 8; ++i) acc[i] = fmaf(f[i], w, acc[i]);
+              for (int i = 0; i < 8; ++i) acc[i] = fmaf(f[i], wv, acc[i]);
             }
           }
         }
       }
-      if (g < RG) {
-        float4 *pp = reinterpret_cast<float4 *>(part + (int64_t)g * nc + col);
-        pp[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        pp[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      if (eg < EG) {
+        float4 *pp = reinterpret_cast<float4 *>(part + (int64_t)eg * nc + ecol);
+        pp[0] = make_float4(acc[0] - cmp[0], acc[1] - cmp[1], acc[2] - cmp[2], acc[3] - cmp[3]);
+        pp[1] = make_float4(acc[4] - cmp[4], acc[5] - cmp[5], acc[6] - cmp[6], acc[7] - cmp[7]);
       }
-      csync();
-      if (staged && tid == 0) mbar_arrive(empty_y0 + 8 * (h % ns));  // Y slot free again
+    }
+    if (!inc_e && tid == 0 && !wait_or_abort(bar_u + 8 * (sh - 1), upar, vab, false))
+      atomicOr(&s_abort, 1);
+    csync();
+    if (s_abort) { abort = true; break; }
+    if (gmode == G_STEP && sh >= 2 && tid == 0) mbar_arrive(empty_g0 + 8 * (h & 1));
+
+    // ---- E: x <- c^{sh} x - alpha c^{sh-1} Y^T (c^{-j} u), own slice ---------
+    {
       const float decay = (float)cpw[sh];
       const float stp = (float)zcw[sh];
-      // TPC threads per column (consecutive lanes), each Kahan-summing RG/TPC
-      // row-group partials, then a shuffle tree across the TPC lanes
-      const int TPC = nc >= kCThreads ? 1 : kCThreads / nc;
-      for (int c0 = 0; c0 < nc; c0 += kCThreads / TPC) {
-        const int c = c0 + tid / TPC, q = tid % TPC;
-        float S = 0.f, cS = 0.f;
-        if (c < nc) {
-          for (int gg = q; gg < RG; gg += TPC) {
-            const float yv = part[(int64_t)gg * nc + c] - cS;
-            const float t2 = S + yv;
-            cS = (t2 - S) - yv;
-            S = t2;
+      if (emode != 2) {
+        if (emode == 1) {  // row groups of every consumer thread, rows in order
+          const int g = tid / V, v = tid - (tid / V) * V;
+          const int64_t col = (int64_t)v * 8;
+          float acc[8], cmp[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) { acc[i] = 0.f; cmp[i] = 0.f; }
+          if (g < EG && col0 + col < n) {
+            for (int64_t r = g; r < R; r += EG) {
+              Raw8<TY> raw;
+              raw.load(Ys + r * ystride + col, staged);
+              float f[8];
+              raw.get(f);
+              const float wv = (float)uh[r];
+              if (a.kahan) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  const float yv = fmaf(f[i], wv, -cmp[i]);
+                  const float t2 = acc[i] + yv;
+                  cmp[i] = (t2 - acc[i]) - yv;
+                  acc[i] = t2;
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = fmaf(f[i], wv, acc[i]);
+              }
+            }
+          }
+          if (g < EG) {
+            float4 *pp = reinterpret_cast<float4 *>(part + (int64_t)g * nc + col);
+            pp[0] = make_float4(acc[0] - cmp[0], acc[1] - cmp[1], acc[2] - cmp[2], acc[3] - cmp[3]);
+            pp[1] = make_float4(acc[4] - cmp[4], acc[5] - cmp[5], acc[6] - cmp[6], acc[7] - cmp[7]);
+          }
+          csync();
+        }
+        if (staged && tid == 0) mbar_arrive(empty_y0 + 8 * (h % ns));  // Y slot free again
+        // TPC threads per column (consecutive lanes), each Kahan-summing EG/TPC
+        // row-group partials, then a shuffle tree across the TPC lanes
+        const int TPC = nc >= kCThreads ? 1 : kCThreads / nc;
+        for (int c0 = 0; c0 < nc; c0 += kCThreads / TPC) {
+          const int c = c0 + tid / TPC, q = tid % TPC;
+          float S = 0.f, cS = 0.f;
+          if (c < nc) {
+            for (int gg = q; gg < EG; gg += TPC) {
+              const float yv = part[(int64_t)gg * nc + c] - cS;
+              const float t2 = S + yv;
+              cS = (t2 - S) - yv;
+              S = t2;
+            }
+          }
+          S -= cS;
+          for (int off = (TPC < 32 ? TPC : 32) / 2; off > 0; off >>= 1)
+            S += __shfl_xor_sync(0xffffffffu, S, off);
+          if (TPC > 32) {  // more than a warp per column (only nc = 8)
+            __shared__ float wred[kCWarps];
+            if (lane == 0) wred[warp] = S;
+            csync();
+            if (q == 0 && c < nc) {
+              S = 0.f;
+              for (int w = 0; w < TPC / 32; ++w) S += wred[(tid / 32) + w];
+            }
+            csync();
+          }
+          if (q == 0 && c < nc && col0 + c < n) {
+            const float xn = fmaf(-stp, S, decay * xs[c]);
+            if (!isfinite(xn)) atomicOr(flag, FLAG_NONFINITE);
+            xs[c] = xn;
           }
         }
-        S -= cS;
-        for (int off = (TPC < 32 ? TPC : 32) / 2; off > 0; off >>= 1)
-          S += __shfl_xor_sync(0xffffffffu, S, off);
-        if (TPC > 32) {  // more than a warp per column (only nc = 8)
-          __shared__ float wred[kCWarps];
-          if (lane == 0) wred[warp] = S;
-          csync();
-          if (q == 0 && c < nc) {
-            S = 0.f;
-            for (int w = 0; w < TPC / 32; ++w) S += wred[(tid / 32) + w];
+      } else {
+        // wide slices (more vectors than consumer threads): one thread per vector
+        // sums every row of the step in order, after the recurrence
+        for (int v = tid; v < V; v += kCThreads) {
+          const int64_t col = (int64_t)v * 8;
+          if (col0 + col >= n) continue;
+          float acc[8], cmp[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) { acc[i] = 0.f; cmp[i] = 0.f; }
+          for (int64_t r = 0; r < R; ++r) {
+            Raw8<TY> raw;
+            raw.load(Ys + r * ystride + col, staged);
+            float f[8];
+            raw.get(f);
+            const float wv = (float)uh[r];
+            if (a.kahan) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float yv = fmaf(f[i], wv, -cmp[i]);
+                const float t2 = acc[i] + yv;
+                cmp[i] = (t2 - acc[i]) - yv;
+                acc[i] = t2;
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) acc[i] = fmaf(f[i], wv, acc[i]);
+            }
           }
-          csync();
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (col0 + col + i < n) {
+              const float xn = fmaf(-stp, acc[i] - cmp[i], decay * xs[col + i]);
+              if (!isfinite(xn)) atomicOr(flag, FLAG_NONFINITE);
+              xs[col + i] = xn;
+            }
+          }
         }
-        if (q == 0 && c < nc && col0 + c < n) {
-          const float xn = fmaf(-stp, S, decay * xs[c]);
-          if (!isfinite(xn)) atomicOr(flag, FLAG_NONFINITE);
-          xs[c] = xn;
-        }
+        csync();
+        if (staged && tid == 0) mbar_arrive(empty_y0 + 8 * (h % ns));  // Y slot free again
       }
       csync();
     }

@@ -119,6 +119,24 @@ def test_ca_fp64_recurrence_and_graph_off(G, c1):
             assert _rel(x, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("n,cluster,rec", [
+    (5000, 1, 0),   # 1024 eight-column vectors per CTA: one thread per vector, after the recurrence
+    (3500, 1, 0),   # 512 vectors, more than the update warps: every consumer thread, after
+    (600, 2, 1),    # FP64 recurrence, 12 own rows: every consumer warp runs rows
+    (600, 8, 1),    # FP64 recurrence, 3 own rows: three row warps, the update folded in
+    (600, 2, 0),    # FP32, three groups of four own rows, 16-byte residual stores
+    (600, 8, 0),    # FP32, 3 own rows: one partial group, per-row residual stores
+])
+def test_update_and_row_warp_layouts(G, n, cluster, rec):
+    pr = synth.ragged(1500, n, seed=n + cluster, loss=synth.LOGISTIC, lam=1e-3)
+    b, s, iters, eta = 24, 4, 96, 0.25
+    ds = _ds(G, pr)
+    ref = oracle.sgd(pr.A, pr.y, pr.loss, b, eta, 1e-3, iters, 5)
+    x = _run(G, ds, pr, s, b, eta, 1e-3, iters, 5, gram_dtype="f32", cluster=cluster,
+             recurrence_f64=rec)
+    assert _rel(x, ref) <= 1e-5
+
+
 @pytest.mark.parametrize("storage,gram", [("f32", "f32"), ("bf16", "bf16")])
 def test_ca_large_block_unstaged(G, storage, gram):
     # s*b = 1024 rows of n = 1024: the per-CTA slice of one outer step does not
