@@ -15,14 +15,15 @@
 //
 // Warp roles in each CTA: 16 consumer warps do the arithmetic above and
 // synchronise among themselves only (named barrier 1).  During the
-// recurrence, up to four row warps (warps 0 mod 4) each own groups of four
-// rows and run the serial loop, while the twelve other consumer warps fold
-// each block's Y_j^T u_j into the update as soon as it lands.  One producer warp
-// streams everything x-independent into shared memory ahead of use -- the
-// CTA's column slice of the rows of Y and their labels (TMA 2D tiles and a
-// bulk copy, `ns` outer steps in flight) and the own rows of G_{j,<j} (bulk
-// copies; a whole outer step ahead when two steps fit, else one block row
-// ahead) -- gated by full / empty mbarriers.  x-dependent values travel one
+// recurrence, the first few consumer warps each run the serial loop for own
+// rows dealt to them round-robin, while the others fold each block's
+// Y_j^T u_j into the update as soon as it lands.  Everything x-independent
+// is streamed into shared memory ahead of use -- the CTA's column slice of
+// the rows of Y and their labels (TMA 2D tiles and a bulk copy, `ns` outer
+// steps in flight) and the own rows of G_{j,<j} (bulk copies; a whole outer
+// step ahead when two steps fit, else one block row ahead) -- by one thread
+// that issues each copy once its slot is known to be free, behind full
+// mbarriers.  x-dependent values travel one
 // way: (vector) st.async into the owner's shared memory, completing
 // transaction bytes on the owner's mbarrier (one per block of residuals), so
 // an inner step costs one DSMEM latency and no cluster or CTA barrier.
@@ -44,17 +45,17 @@ namespace {
 
 constexpr int kCThreads = 512;              // consumer threads (warps 0..15)
 constexpr int kCWarps = kCThreads / 32;
-constexpr int kThreads = kCThreads + 32;    // + one producer warp
-constexpr int kWThreads = kCThreads - kCWarps / 4 * 32;  // update workers: warps w % 4 != 0
+constexpr int kThreads = kCThreads;         // 16 warps: 128 registers a thread
 constexpr long long kWaitBudget = 4000000000ll;  // SM cycles (~2 s)
 constexpr size_t kSmemMax = 227 * 1024 - 2048;  // leave room for static shared memory
-constexpr int kMaxSlots = 4;
+constexpr int kMaxSlots = 4;   // Y slots
+constexpr int kMaxGSlots = 4;  // G slots of one block row each
 
 enum { G_NONE = 0, G_STEP = 2, G_BLOCK = 3 };
 
 struct Layout {
-  int nc, rpb, C, gmode, ns, box_rows, nbox;
-  int64_t gslot_floats;    // floats per G slot (two slots)
+  int nc, rpb, C, gmode, ns, ngs, box_rows, nbox;
+  int64_t gslot_floats;    // floats per G slot (ngs slots)
   int64_t ylab_off;        // byte offset of the labels inside a Y slot
   int64_t yslot;           // bytes per Y slot
   size_t off_uh, off_rrecv, off_rown, off_yown, off_part, off_bar, off_coef,
@@ -99,22 +100,29 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t b, int s, int C
   L.gmode = G_NONE;
   L.ns = 0;
   L.gslot_floats = 0;
-  auto fits = [&](int64_t gfl, int ns) {
-    const size_t g_end = round_up(base, 16) + 2 * (size_t)gfl * 4;
+  L.ngs = 2;
+  auto fits = [&](int64_t gfl, int ngs, int ns) {
+    const size_t g_end = round_up(base, 16) + (size_t)ngs * gfl * 4;
     return round_up(g_end, 1024) + (size_t)ns * L.yslot + (ns ? 1024 : 0) <= kSmemMax;
   };
   const int gm[3] = {G_STEP, G_BLOCK, G_NONE};
   const int64_t gf[3] = {g_step, g_blk, 0};
   bool done = false;
-  for (int ns = kMaxSlots; ns >= 2 && ystage && !done; --ns)
-    for (int q = 0; q < 3 && !done; ++q)
-      if ((q == 2 || s >= 2) && fits(gf[q], ns)) {
-        L.ns = ns; L.gmode = gm[q]; L.gslot_floats = gf[q]; done = true;
-      }
+  // staged G first (the recurrence reads it on the critical path): a whole
+  // step per slot (two slots), else one block row per slot with as many
+  // slots (up to kMaxGSlots, the refill lead) as fit; then as many Y slots
+  auto pick = [&](int q, int ngs, int ns) {
+    L.ns = ns; L.gmode = gm[q]; L.gslot_floats = gf[q]; L.ngs = ngs; done = true;
+  };
+  for (int q = 0; q < 3 && ystage && !done; ++q)
+    for (int ngs = (q == 1 ? kMaxGSlots : 2); ngs >= 2 && !done; --ngs)
+      for (int ns = kMaxSlots; ns >= 2 && !done; --ns)
+        if ((q == 2 || s >= 2) && fits(gf[q], ngs, ns)) pick(q, ngs, ns);
   for (int q = 0; q < 2 && !done && want_prefetch && s >= 2; ++q)
-    if (fits(gf[q], 0)) { L.gmode = gm[q]; L.gslot_floats = gf[q]; done = true; }
+    for (int ngs = (q == 1 ? kMaxGSlots : 2); ngs >= 2 && !done; --ngs)
+      if (fits(gf[q], ngs, 0)) pick(q, ngs, 0);
   off = base;
-  L.off_gbuf = take(2 * (size_t)L.gslot_floats * 4, 16);
+  L.off_gbuf = take((size_t)L.ngs * L.gslot_floats * 4, 16);
   L.off_ybuf = take(L.ns ? (size_t)L.ns * L.yslot : 0, 1024);
   L.total = off + (L.ns ? 1024 : 0);  // slack to 1024-align the Y slots at run time
   return L;
@@ -300,21 +308,26 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const int s = a.s;
   const int64_t sb = (int64_t)s * b;
   const Layout L = make_layout(n, b, s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
-  const int nc = L.nc, rpb = L.rpb, ns = L.ns, gmode = L.gmode;
+  const int nc = L.nc, rpb = L.rpb, ns = L.ns, gmode = L.gmode, ngs = L.ngs;
   const int64_t col0 = (int64_t)rank * nc;
   const int64_t l0 = (int64_t)rank * rpb;
   const int nown = (int)max((int64_t)0, min((int64_t)rpb, b - l0));
-  // Recurrence row warps, each taking its own rows four at a time.  FP32:
-  // warps 0, 4, 8, 12 (one SM sub-partition, which no worker warp shares)
-  // with contiguous groups, so a group's residuals leave as one 16-byte store.
-  // FP64: rows dealt round-robin to warps 0, 1, 2, ... so that the FP64
-  // work spreads over every sub-partition (the FP64 pipe is the bound
-  // there): up to four row warps, leaving warps 4..15 to the update, or,
-  // with more than four own rows, every consumer warp (the update then
-  // follows the recurrence).
+  // Recurrence row warps.  FP32: up to four, warps 0, 4, 8, 12 (the SM
+  // sub-partition of warp id 0 mod 4, which no worker warp shares), each
+  // finishing contiguous groups of four own rows, so that a group's
+  // residuals leave as one 16-byte store per destination CTA; the other
+  // twelve warps fold the update in.  FP64 (whose pipe is the bound): own
+  // rows dealt one at a time, round-robin, to warps 0, 1, 2, 3 (one per
+  // sub-partition) with the update folded in by warps 4..15, or, with more
+  // than four own rows, to every consumer warp, the update following.
   constexpr bool kF64 = sizeof(TR) == 8;
   const bool all_rows = kF64 && nown > 4;
   const int nrw = kF64 ? min(nown, kCWarps) : min((nown + 3) / 4, 4);
+  const int nwt = all_rows ? 0 : 3 * kCThreads / 4;  // worker threads
+  const int rw = kF64 ? (warp < nrw ? warp : -1)     // row warp index, or -1
+                      : ((warp & 3) == 0 && (warp >> 2) < nrw ? warp >> 2 : -1);
+  const int wbase_t = kF64 ? (warp >= 4 && !all_rows ? (warp - 4) * 32 : -1)
+                           : ((warp & 3) != 0 ? (warp - (warp >> 2) - 1) * 32 : -1);
 
   extern __shared__ __align__(1024) unsigned char smem[];
   float *xs = reinterpret_cast<float *>(smem);
@@ -331,19 +344,20 @@ k_chain(const __grid_constant__ ChainArgs a) {
   TR *zcw = cinw + (s + 1);                                // alpha c^(j-1), j >= 1
   uint32_t *rem = reinterpret_cast<uint32_t *>(smem + L.off_rem);
   __shared__ int s_abort;
+  __shared__ int s_fills[kMaxSlots + kMaxGSlots];  // copies issued per Y slot, then G slot
 
   const uint32_t bar0 = smem_u32(smem + L.off_bar);
   const uint32_t bar_r = bar0;                       // margin partials
   const uint32_t bar_u = bar0 + 8 * 16;              // residuals of block j: + 8 j
-  const uint32_t full_g0 = bar0 + 24, empty_g0 = bar0 + 40;   // x2 each
-  const uint32_t full_y0 = bar0 + 56, empty_y0 = bar0 + 88;   // x kMaxSlots each
+  const uint32_t full_g0 = bar0 + 24;                // G slots (x ngs <= 4)
+  const uint32_t full_y0 = bar0 + 56;                // Y slots (x kMaxSlots)
 
   if (tid == 0) {
-    for (int i = 0; i < 15; ++i)  // G_BLOCK: every row warp releases a G slot
-      mbar_init(bar0 + 8 * i, (gmode == G_BLOCK && i >= 5 && i < 7) ? nrw : 1);
+    for (int i = 0; i < 15; ++i) mbar_init(bar0 + 8 * i, 1);
     for (int j = 0; j < s; ++j) mbar_init(bar_u + 8 * j, 1);
     fence_mbar_init_cluster();
     s_abort = 0;
+    for (int k = 0; k < kMaxSlots + kMaxGSlots; ++k) s_fills[k] = 0;
   }
   for (int j = tid; j <= s; j += kThreads) {
     cpw[j] = (TR)a.cpow[j];
@@ -358,98 +372,71 @@ k_chain(const __grid_constant__ ChainArgs a) {
   }
   for (int c = tid; c < nc; c += kThreads) xs[c] = (col0 + c < n) ? a.x[col0 + c] : 0.f;
   const int64_t gsz = gram_size(s, b);
+
+  // ---- x-independent copies into shared memory --------------------------
+  // One thread at a time issues them, each at a point where its target slot
+  // is known to be free (no empty barriers): the Y slot of step h - 1 once
+  // step h has begun, a G slot once the residuals of the block that read it
+  // have landed from every CTA (our own row warps sent theirs after reading
+  // it).  Each copy completes transaction bytes on its slot's full barrier.
+  const uint32_t ystep_bytes =
+      (uint32_t)((int64_t)L.nbox * L.box_rows * nc * sizeof(TY) + round_up(sb, 4) * 4);
+  const int64_t nblk = gmode == G_BLOCK
+                           ? (int64_t)(a.nouter - 1) * (s - 1) + max(a.s_last - 1, 0)
+                           : 0;  // staged G block rows (j >= 1) of the launch
+  auto issue_y = [&](int hh) {  // Y slice and labels of step hh
+    if (ns == 0 || hh >= a.nouter) return;
+    const int slot = hh % ns;
+    const uint32_t bar = full_y0 + 8 * slot;
+    const uint32_t dst = smem_u32(ybuf + (int64_t)slot * L.yslot);
+    mbar_arrive_expect_tx(bar, ystep_bytes);
+    for (int k = 0; k < L.nbox; ++k)
+      tma_load_2d(dst + (uint32_t)((int64_t)k * L.box_rows * nc * sizeof(TY)), &a.ymap,
+                  (int32_t)col0, (int32_t)((int64_t)hh * sb + (int64_t)k * L.box_rows), bar);
+    bulk_load(dst + (uint32_t)L.ylab_off, a.ylab + (int64_t)hh * a.sbp,
+              (uint32_t)(round_up(sb, 4) * 4), bar);
+    ++s_fills[slot];
+  };
+  auto issue_gs = [&](int hh) {  // G_STEP: own rows of every block row of step hh
+    if (gmode != G_STEP || hh >= a.nouter) return;
+    const int shh = (hh == a.nouter - 1) ? a.s_last : s;
+    if (shh < 2) return;
+    const int slot = hh & 1;
+    const uint32_t bar = full_g0 + 8 * slot;
+    const float *Gs = a.G + (int64_t)hh * gsz;
+    const uint32_t dst = smem_u32(gbuf + slot * L.gslot_floats);
+    int64_t bytes = 0;
+    for (int j = 1; j < shh; ++j) bytes += (int64_t)nown * gram_ld(j, b) * 4;
+    mbar_arrive_expect_tx(bar, (uint32_t)bytes);
+    int64_t soff = 0;  // floats into the slot
+    for (int j = 1; j < shh; ++j) {
+      const int64_t ldj = gram_ld(j, b);
+      bulk_load(dst + (uint32_t)(soff * 4), Gs + gram_off(j, b) + l0 * ldj,
+                (uint32_t)(nown * ldj * 4), bar);
+      soff += (int64_t)rpb * ldj;
+    }
+    ++s_fills[kMaxSlots + slot];
+  };
+  auto issue_gb = [&](int64_t kb) {  // G_BLOCK: block row kb of the launch (j >= 1 rows)
+    if (gmode != G_BLOCK || kb >= nblk) return;
+    const int hh = (int)(kb / (s - 1)), j = (int)(kb % (s - 1)) + 1;
+    const int slot = (int)(kb % ngs);
+    const int64_t ldj = gram_ld(j, b);
+    const uint32_t bar = full_g0 + 8 * slot;
+    mbar_arrive_expect_tx(bar, (uint32_t)(nown * ldj * 4));
+    bulk_load(smem_u32(gbuf + slot * L.gslot_floats),
+              a.G + (int64_t)hh * gsz + gram_off(j, b) + l0 * ldj, (uint32_t)(nown * ldj * 4), bar);
+    ++s_fills[kMaxSlots + slot];
+  };
+  if (tid == 0 && ns > 0)  // the Y tensor map is read by every Y fill
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&a.ymap)) : "memory");
   // barriers initialised in every CTA before any remote traffic
   cluster.sync();
-
-  // ========================= producer warp ===================================
-  if (warp == kCWarps) {
-    if (lane == 0) {
-      const uint32_t ystep_bytes =
-          (uint32_t)((int64_t)L.nbox * L.box_rows * nc * sizeof(TY) + round_up(sb, 4) * 4);
-      int64_t kblk = 0;          // G block rows issued so far (G_BLOCK mode)
-      int y_iss = 0, g_iss = 0;  // copies issued (for the abort drain)
-      volatile int *vabort = &s_abort;
-      for (int hh = 0; hh < a.nouter && !*vabort; ++hh) {
-        const int shh = (hh == a.nouter - 1) ? a.s_last : s;
-        if (ns) {
-          const int slot = hh % ns;
-          if (hh >= ns && !mbar_wait_sleep(empty_y0 + 8 * slot,
-                                             (uint32_t)((hh / ns - 1) & 1), kWaitBudget)) {
-            atomicOr(&s_abort, 1);
-            break;
-          }
-          const uint32_t bar = full_y0 + 8 * slot;
-          const uint32_t dst = smem_u32(ybuf + (int64_t)slot * L.yslot);
-          mbar_arrive_expect_tx(bar, ystep_bytes);
-          for (int k = 0; k < L.nbox; ++k)
-            tma_load_2d(dst + (uint32_t)((int64_t)k * L.box_rows * nc * sizeof(TY)), &a.ymap,
-                        (int32_t)col0, (int32_t)((int64_t)hh * sb + (int64_t)k * L.box_rows),
-                        bar);
-          bulk_load(dst + (uint32_t)L.ylab_off, a.ylab + (int64_t)hh * a.sbp,
-                    (uint32_t)(round_up(sb, 4) * 4), bar);
-          ++y_iss;
-        }
-        if (gmode == G_STEP && shh >= 2) {
-          const int slot = hh & 1;
-          if (hh >= 2 && !mbar_wait_sleep(empty_g0 + 8 * slot,
-                                            (uint32_t)(((hh >> 1) - 1) & 1), kWaitBudget)) {
-            atomicOr(&s_abort, 1);
-            break;
-          }
-          const uint32_t bar = full_g0 + 8 * slot;
-          const float *Gh = a.G + (int64_t)hh * gsz;
-          const uint32_t dst = smem_u32(gbuf + slot * L.gslot_floats);
-          int64_t bytes = 0;
-          for (int j = 1; j < shh; ++j) bytes += (int64_t)nown * gram_ld(j, b) * 4;
-          mbar_arrive_expect_tx(bar, (uint32_t)bytes);
-          int64_t soff = 0;  // floats into the slot
-          for (int j = 1; j < shh; ++j) {
-            const int64_t ldj = gram_ld(j, b);
-            bulk_load(dst + (uint32_t)(soff * 4), Gh + gram_off(j, b) + l0 * ldj,
-                      (uint32_t)(nown * ldj * 4), bar);
-            soff += (int64_t)rpb * ldj;
-          }
-          ++g_iss;
-        } else if (gmode == G_BLOCK) {
-          const float *Gh = a.G + (int64_t)hh * gsz;
-          bool stop = false;
-          for (int j = 1; j < shh; ++j, ++kblk) {
-            const int slot = (int)(kblk & 1);
-            // a refill is one block ahead of the recurrence: spin (with short
-            // naps) rather than let the hardware suspend this thread
-            if (kblk >= 2 && !wait_or_abort(empty_g0 + 8 * slot,
-                                            (uint32_t)(((kblk >> 1) - 1) & 1), vabort, true)) {
-              atomicOr(&s_abort, 1);
-              stop = true;
-              break;
-            }
-            const int64_t ldj = gram_ld(j, b);
-            const uint32_t bar = full_g0 + 8 * slot;
-            mbar_arrive_expect_tx(bar, (uint32_t)(nown * ldj * 4));
-            bulk_load(smem_u32(gbuf + slot * L.gslot_floats), Gh + gram_off(j, b) + l0 * ldj,
-                      (uint32_t)(nown * ldj * 4), bar);
-            ++g_iss;
-          }
-          if (stop) break;
-        }
-      }
-      if (*vabort) {
-        // wait (bounded) until every copy this warp issued has landed: the
-        // i-th fill of a two-phase slot completes phase i, so the last fill
-        // of each slot is awaited with the parity of its own phase
-        for (int k = 0; k < ns && k < y_iss; ++k) {
-          const int last = ((y_iss - 1 - k) / ns) * ns + k;  // last fill of slot k
-          mbar_wait_bounded(full_y0 + 8 * k, (uint32_t)((last / ns) & 1), kWaitBudget);
-        }
-        for (int k = 0; k < 2 && k < g_iss; ++k) {
-          const int last = ((g_iss - 1 - k) / 2) * 2 + k;
-          mbar_wait_bounded(full_g0 + 8 * k, (uint32_t)((last / 2) & 1), kWaitBudget);
-        }
-      }
-    }
-    __syncwarp();
-    cluster.sync();
-    return;
+  if (tid == 0) {  // fill every Y slot and both G slots
+    for (int hh = 0; hh < ns; ++hh) issue_y(hh);
+    issue_gs(0);
+    issue_gs(1);
+    for (int kb = 0; kb < ngs; ++kb) issue_gb(kb);
   }
 
   // ========================= consumer warps ==================================
@@ -464,6 +451,14 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const TY *Y = static_cast<const TY *>(a.Y);
   int64_t kblk = 0;       // G block rows consumed (G_BLOCK mode)
   bool abort = false;
+  // update: 0 = folded in block by block by the workers, 1 = after the
+  // recurrence by every consumer thread (row groups), 2 = after the
+  // recurrence, one thread per 8-column vector (slices wider than that)
+  const int emode = (nwt > 0 && V <= nwt) ? 0 : (V <= kCThreads ? 1 : 2);
+  const bool inc_e = emode == 0;
+  const int EG = emode == 0 ? nwt / V : (emode == 1 ? kCThreads / V : 1);  // row groups
+  // copies are issued by worker thread 0 when workers fold the update in,
+  // else by thread 0
 
   for (int h = 0; h < a.nouter && !abort; ++h) {
     const int sh = (h == a.nouter - 1) ? a.s_last : s;
@@ -474,6 +469,10 @@ k_chain(const __grid_constant__ ChainArgs a) {
     if (warp == 0)  // every block's residuals: b values from the whole cluster
       for (int j = lane; j < sh; j += 32)
         mbar_arrive_expect_tx(bar_u + 8 * j, (uint32_t)(b * sizeof(TR)));
+    if (!inc_e && tid == 0 && h >= 1) {  // into step h - 1's slots
+      issue_y(h + ns - 1);
+      issue_gs(h + 1);
+    }
     const bool staged = ns > 0;
     const TY *Ys;          // row r of this CTA's slice at Ys + r * ystride
     int64_t ystride;
@@ -589,23 +588,14 @@ k_chain(const __grid_constant__ ChainArgs a) {
     if (s_abort) { abort = true; break; }
 
     // ---- D + E: recurrence on the row warps, update on the worker warps ----
-    // Row warps run the serial loop over blocks.  Block j of every CTA lands on this CTA's barrier bar_u[j]; a row warp
-    // waits on it before block j + 1, and the worker warps (w % 4 != 0) wait
-    // on it before folding Y_j^T (c^{-j} u_j) into their Kahan sums, so the
-    // update runs under the recurrence instead of after it.  Workers: the
-    // twelve consumer warps that are not row-warp candidates.
+    // Row warps run the serial loop over blocks.  Block j of every CTA lands
+    // on this CTA's barrier bar_u[j]; a row warp waits on it before block
+    // j + 1, and the worker warps wait on it before folding Y_j^T (c^{-j} u_j)
+    // into their Kahan sums, so the update runs under the recurrence
+    // instead of after it.
     const uint32_t upar = (uint32_t)(h & 1);
     const volatile int *vab = &s_abort;
-    // update: 0 = folded in block by block by the workers, 1 = after the
-    // recurrence by every consumer thread (row groups), 2 = after the
-    // recurrence, one thread per 8-column vector (slices wider than that)
-    const int emode = (!all_rows && V <= kWThreads) ? 0 : (V <= kCThreads ? 1 : 2);
-    const bool inc_e = emode == 0;
-    const int EG = emode == 0 ? kWThreads / V : (emode == 1 ? kCThreads / V : 1);  // row groups
-    const bool row_warp = kF64 ? warp < nrw : ((warp & 3) == 0 && (warp >> 2) < nrw);
-    const bool worker = kF64 ? (warp >= 4 && !all_rows) : (warp & 3) != 0;
-    if (row_warp) {
-      const int rw = kF64 ? warp : warp >> 2;
+    if (rw >= 0) {
       const uint32_t ra_u = lane < C ? rem[32 + lane] : 0u;  // CTA lane's residual history
       const uint32_t rb_u = lane < C ? rem[48 + lane] : 0u;  // and its block barriers
       {
@@ -614,39 +604,41 @@ k_chain(const __grid_constant__ ChainArgs a) {
           const int64_t ldj = gram_ld(j, b);
           int64_t gofs = 0;  // float offset of this block row's own rows
           if (j > 0) {
-            // lane 0 polls (a whole warp of probes would load the shared-memory
-            // pipe the other lanes' reads depend on); the warp then follows
+            // lane 0 polls; the warp follows
             int ok = 1;
             if (lane == 0) {
               ok = wait_or_abort(bar_u + 8 * (j - 1), upar, vab, false);
               if (ok && gmode == G_BLOCK)
-                ok = wait_or_abort(full_g0 + 8 * (kblk & 1), (uint32_t)((kblk >> 1) & 1), vab,
-                                   false);
+                ok = wait_or_abort(full_g0 + 8 * (int)(kblk % ngs),
+                                   (uint32_t)((kblk / ngs) & 1), vab, false);
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) {
               if (lane == 0) atomicOr(&s_abort, 1);
               break;
             }
+            // block j - 1 has landed everywhere: its G slot takes the block
+            // row ngs further on
+            if (!inc_e && tid == 0 && gmode == G_BLOCK && j >= 2)
+              issue_gb((int64_t)h * (s - 1) + (j - 2) + ngs);
             if (gmode == G_STEP) {
               gofs = (h & 1) * L.gslot_floats + goff;
               goff += (int64_t)rpb * ldj;
             } else if (gmode == G_BLOCK) {
-              gofs = (kblk & 1) * L.gslot_floats;
+              gofs = (kblk % ngs) * L.gslot_floats;
             } else {
               gofs = gram_off(j, b) + l0 * ldj;
             }
           }
           const int jb = (int)(j * b);
           const TR cj = cpw[j], zj = zcw[j], ij = cinw[j];
-          if constexpr (kF64) {  // one row at a time, rows rw, rw + nrw, ...
-            for (int rq = rw; rq < nown; rq += nrw) {
+          if constexpr (kF64) {
+            for (int rq = rw; rq < nown; rq += nrw) {  // own rows rw, rw + nrw, ...
               const TR rv = rown[j * rpb + rq];
               const TR yv = (TR)yown[j * rpb + rq];
               TR corr = 0;
               if (j > 0) {
-                corr = gmode != G_NONE
-                           ? row_dot1<TR, true>(gbuf + gofs + rq * ldj, uh, jb, lane)
-                           : row_dot1<TR, false>(Gh + gofs + rq * ldj, uh, jb, lane);
+                corr = gmode != G_NONE ? row_dot1<TR, true>(gbuf + gofs + rq * ldj, uh, jb, lane)
+                                       : row_dot1<TR, false>(Gh + gofs + rq * ldj, uh, jb, lane);
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1)
                   corr += __shfl_xor_sync(0xffffffffu, corr, off);
@@ -654,14 +646,13 @@ k_chain(const __grid_constant__ ChainArgs a) {
               const TR z = cj * rv - zj * corr;
               const TR u = dloss<TR>(loss_kind, z, yv);
               if (lane == 0 && (!isfinite(z) || !isfinite(u))) atomicOr(flag, FLAG_NONFINITE);
-              if (lane < C)
+              if (lane < C)  // fan-out: lane d writes CTA d's copy of the residual
                 st_async(ra_u + (uint32_t)((jb + l0 + rq) * sizeof(TR)), u * ij, rb_u + 8 * j);
             }
-          } else {  // FP32: contiguous groups of four rows
+          } else {
             for (int q0 = 4 * rw; q0 < nown; q0 += 4 * nrw) {
               // rows q0 + i, i < nq; lane L finishes row L >> 3
               const int nq = min(4, nown - q0);
-              const int64_t rs = ldj;
               const int q = lane >> 3;
               const int rq = q0 + (q < nq ? q : nq - 1);
               const TR rv = rown[j * rpb + rq];
@@ -669,9 +660,9 @@ k_chain(const __grid_constant__ ChainArgs a) {
               TR acc[4] = {0, 0, 0, 0};
               if (j > 0) {
                 if (gmode != G_NONE)
-                  rows_dot4<TR, true>(gbuf + gofs + q0 * ldj, rs, nq, uh, jb, lane, acc);
+                  rows_dot4<TR, true>(gbuf + gofs + q0 * ldj, ldj, nq, uh, jb, lane, acc);
                 else
-                  rows_dot4<TR, false>(Gh + gofs + q0 * ldj, rs, nq, uh, jb, lane, acc);
+                  rows_dot4<TR, false>(Gh + gofs + q0 * ldj, ldj, nq, uh, jb, lane, acc);
               }
               const TR corr = warp_sum4_t(acc, lane);
               const TR z = cj * rv - zj * corr;
@@ -682,7 +673,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
               TR w[4];
 #pragma unroll
               for (int i = 0; i < 4; ++i) w[i] = __shfl_sync(0xffffffffu, uw, 8 * i);
-              if (lane < C) {  // fan-out: lane d writes CTA d's copy of block j
+              if (lane < C) {  // fan-out: lane d writes CTA d's copy of the group
                 const uint32_t ra = ra_u + (uint32_t)((jb + l0 + q0) * sizeof(TR));
                 const uint32_t rb = rb_u + 8 * j;
                 if (vsend_r && nq == 4) {
@@ -695,15 +686,11 @@ k_chain(const __grid_constant__ ChainArgs a) {
               }
             }
           }
-          if (gmode == G_BLOCK && j > 0) {  // this warp is done with the G block row
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty_g0 + 8 * (kblk & 1));
-            ++kblk;
-          }
+          if (gmode == G_BLOCK && j > 0) ++kblk;
         }
       }
-    } else if (worker && inc_e) {
-      const int wt = (kF64 ? warp - 4 : warp - (warp >> 2) - 1) * 32 + lane;  // worker index
+    } else if (wbase_t >= 0 && inc_e) {
+      const int wt = wbase_t + lane;  // worker index
       const int eg = wt / V, ev = wt - (wt / V) * V;
       const int64_t ecol = (int64_t)ev * 8;
       float acc[8], cmp[8];
@@ -712,19 +699,28 @@ k_chain(const __grid_constant__ ChainArgs a) {
       // every worker with rows waits on every block (thread 0 always does, so
       // each phase of bar_u is observed before the next step re-arms it)
       const bool cols = col0 + ecol < n;
+      const bool rows = eg < EG && eg < b;
+      // lane 0 of the first three worker warps refills freed slots (see the
+      // issue helpers), each its own kind so that a slow issue (a Y slice:
+      // TMA) never holds back a G block row the recurrence needs next:
+      // 1 = G block rows, 2 = step h - 1's Y slot, 3 = step h - 1's G slot
+      const int role = (lane == 0 && wt < 96) ? (wt >> 5) + 1 : 0;
       // the lanes with rows form a prefix of the warp (groups ascend with the
-      // thread index); the lowest of them polls for all
-      const unsigned act = __ballot_sync(0xffffffffu, eg < EG && eg < b);
-      if (eg < EG && eg < b) {
-        const int leader = __ffs(act) - 1;
+      // thread index) and lane 0 is among the active lanes; it polls for all
+      const unsigned act = __ballot_sync(0xffffffffu, rows || role);
+      if (rows || role) {
         for (int j = 0; j < sh; ++j) {
           int ok = 1;
-          if (lane == leader) ok = wait_or_abort(bar_u + 8 * j, upar, vab, true);
-          if (!__shfl_sync(act, ok, leader)) {
+          if (lane == 0) ok = wait_or_abort(bar_u + 8 * j, upar, vab, true);
+          if (!__shfl_sync(act, ok, 0)) {
             atomicOr(&s_abort, 1);
             break;
           }
-          if (!cols) continue;
+          if (role == 1 && gmode == G_BLOCK && j >= 1)
+            issue_gb((int64_t)h * (s - 1) + (j - 1) + ngs);
+          if (role == 2 && j == 0 && h >= 1) issue_y(h + ns - 1);
+          if (role == 3 && j == 0 && h >= 1) issue_gs(h + 1);
+          if (!cols || !rows) continue;
           for (int64_t r = (int64_t)j * b + eg; r < (int64_t)(j + 1) * b; r += EG) {
             Raw8<TY> raw;
             raw.load(Ys + r * ystride + ecol, staged);
@@ -746,17 +742,31 @@ k_chain(const __grid_constant__ ChainArgs a) {
           }
         }
       }
-      if (eg < EG) {
-        float4 *pp = reinterpret_cast<float4 *>(part + (int64_t)eg * nc + ecol);
-        pp[0] = make_float4(acc[0] - cmp[0], acc[1] - cmp[1], acc[2] - cmp[2], acc[3] - cmp[3]);
-        pp[1] = make_float4(acc[4] - cmp[4], acc[5] - cmp[5], acc[6] - cmp[6], acc[7] - cmp[7]);
+      float r[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) r[i] = acc[i] - cmp[i];
+      int pg = eg;  // partial group written
+      if (V < 32) {  // lanes V apart share a column vector: one partial per warp
+        for (int off = V; off < 32; off <<= 1)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) r[i] += __shfl_xor_sync(0xffffffffu, r[i], off);
+        pg = lane < V ? wt >> 5 : EG;
+      }
+      if (pg < EG) {
+        float4 *pp = reinterpret_cast<float4 *>(part + (int64_t)pg * nc + ecol);
+        pp[0] = make_float4(r[0], r[1], r[2], r[3]);
+        pp[1] = make_float4(r[4], r[5], r[6], r[7]);
       }
     }
-    if (!inc_e && tid == 0 && !wait_or_abort(bar_u + 8 * (sh - 1), upar, vab, false))
-      atomicOr(&s_abort, 1);
+    if (!inc_e && tid == 0) {
+      if (!wait_or_abort(bar_u + 8 * (sh - 1), upar, vab, false)) {
+        atomicOr(&s_abort, 1);
+      } else if (gmode == G_BLOCK && sh >= 2) {  // the last block's G slot is free
+        issue_gb((int64_t)h * (s - 1) + (sh - 2) + ngs);
+      }
+    }
     csync();
     if (s_abort) { abort = true; break; }
-    if (gmode == G_STEP && sh >= 2 && tid == 0) mbar_arrive(empty_g0 + 8 * (h & 1));
 
     // ---- E: x <- c^{sh} x - alpha c^{sh-1} Y^T (c^{-j} u), own slice ---------
     {
@@ -797,38 +807,56 @@ k_chain(const __grid_constant__ ChainArgs a) {
           }
           csync();
         }
-        if (staged && tid == 0) mbar_arrive(empty_y0 + 8 * (h % ns));  // Y slot free again
-        // TPC threads per column (consecutive lanes), each Kahan-summing EG/TPC
-        // row-group partials, then a shuffle tree across the TPC lanes
-        const int TPC = nc >= kCThreads ? 1 : kCThreads / nc;
-        for (int c0 = 0; c0 < nc; c0 += kCThreads / TPC) {
-          const int c = c0 + tid / TPC, q = tid % TPC;
-          float S = 0.f, cS = 0.f;
-          if (c < nc) {
-            for (int gg = q; gg < EG; gg += TPC) {
-              const float yv = part[(int64_t)gg * nc + c] - cS;
+        if (emode == 0 && V < 32) {
+          // one partial per worker warp: a thread per column sums them in order
+          if (tid < nc) {
+            float S = 0.f, cS = 0.f;
+            for (int gg = 0; gg < nwt / 32; ++gg) {
+              const float yv = part[(int64_t)gg * nc + tid] - cS;
               const float t2 = S + yv;
               cS = (t2 - S) - yv;
               S = t2;
             }
-          }
-          S -= cS;
-          for (int off = (TPC < 32 ? TPC : 32) / 2; off > 0; off >>= 1)
-            S += __shfl_xor_sync(0xffffffffu, S, off);
-          if (TPC > 32) {  // more than a warp per column (only nc = 8)
-            __shared__ float wred[kCWarps];
-            if (lane == 0) wred[warp] = S;
-            csync();
-            if (q == 0 && c < nc) {
-              S = 0.f;
-              for (int w = 0; w < TPC / 32; ++w) S += wred[(tid / 32) + w];
+            S -= cS;
+            if (col0 + tid < n) {
+              const float xn = fmaf(-stp, S, decay * xs[tid]);
+              if (!isfinite(xn)) atomicOr(flag, FLAG_NONFINITE);
+              xs[tid] = xn;
             }
-            csync();
           }
-          if (q == 0 && c < nc && col0 + c < n) {
-            const float xn = fmaf(-stp, S, decay * xs[c]);
-            if (!isfinite(xn)) atomicOr(flag, FLAG_NONFINITE);
-            xs[c] = xn;
+        } else {
+          // TPC threads per column (consecutive lanes), each Kahan-summing EG/TPC
+          // row-group partials, then a shuffle tree across the TPC lanes
+          const int TPC = nc >= kCThreads ? 1 : kCThreads / nc;
+          for (int c0 = 0; c0 < nc; c0 += kCThreads / TPC) {
+            const int c = c0 + tid / TPC, q = tid % TPC;
+            float S = 0.f, cS = 0.f;
+            if (c < nc) {
+              for (int gg = q; gg < EG; gg += TPC) {
+                const float yv = part[(int64_t)gg * nc + c] - cS;
+                const float t2 = S + yv;
+                cS = (t2 - S) - yv;
+                S = t2;
+              }
+            }
+            S -= cS;
+            for (int off = (TPC < 32 ? TPC : 32) / 2; off > 0; off >>= 1)
+              S += __shfl_xor_sync(0xffffffffu, S, off);
+            if (TPC > 32) {  // more than a warp per column (only nc = 8)
+              __shared__ float wred[kCWarps];
+              if (lane == 0) wred[warp] = S;
+              csync();
+              if (q == 0 && c < nc) {
+                S = 0.f;
+                for (int w = 0; w < TPC / 32; ++w) S += wred[(tid / 32) + w];
+              }
+              csync();
+            }
+            if (q == 0 && c < nc && col0 + c < n) {
+              const float xn = fmaf(-stp, S, decay * xs[c]);
+              if (!isfinite(xn)) atomicOr(flag, FLAG_NONFINITE);
+              xs[c] = xn;
+            }
           }
         }
       } else {
@@ -869,13 +897,25 @@ k_chain(const __grid_constant__ ChainArgs a) {
           }
         }
         csync();
-        if (staged && tid == 0) mbar_arrive(empty_y0 + 8 * (h % ns));  // Y slot free again
       }
       csync();
     }
   }
   if (abort) {
-    if (tid == 0) atomicOr(a.flag, FLAG_TIMEOUT);
+    // every consumer has left the step loop (the exits follow a CTA barrier):
+    // wait (bounded) for the copies still in flight -- only a slot's last
+    // fill can be, and fill i of a slot completes its phase i
+    csync();
+    if (tid == 0) {
+      atomicOr(a.flag, FLAG_TIMEOUT);
+      for (int k = 0; k < ns; ++k)
+        if (s_fills[k] > 0)
+          mbar_wait_bounded(full_y0 + 8 * k, (uint32_t)((s_fills[k] - 1) & 1), kWaitBudget);
+      for (int k = 0; k < ngs; ++k)
+        if (s_fills[kMaxSlots + k] > 0)
+          mbar_wait_bounded(full_g0 + 8 * k, (uint32_t)((s_fills[kMaxSlots + k] - 1) & 1),
+                            kWaitBudget);
+    }
   } else {
     for (int c = tid; c < nc; c += kCThreads)
       if (col0 + c < n) a.x[col0 + c] = xs[c];
