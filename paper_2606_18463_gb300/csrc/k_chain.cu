@@ -705,10 +705,13 @@ k_chain(const __grid_constant__ ChainArgs a) {
       // TMA) never holds back a G block row the recurrence needs next:
       // 1 = G block rows, 2 = step h - 1's Y slot, 3 = step h - 1's G slot
       const int role = (lane == 0 && wt < 96) ? (wt >> 5) + 1 : 0;
-      // the lanes with rows form a prefix of the warp (groups ascend with the
-      // thread index) and lane 0 is among the active lanes; it polls for all
-      const unsigned act = __ballot_sync(0xffffffffu, rows || role);
-      if (rows || role) {
+      // every lane of those three warps follows the block loop (a lone
+      // active lane with the rest of its warp parked is slow); elsewhere the
+      // lanes with rows form a prefix of the warp (groups ascend with the
+      // thread index).  Lane 0 is active whenever any lane is; it polls.
+      const bool active = rows || wt < 96;
+      const unsigned act = __ballot_sync(0xffffffffu, active);
+      if (active) {
         for (int j = 0; j < sh; ++j) {
           int ok = 1;
           if (lane == 0) ok = wait_or_abort(bar_u + 8 * j, upar, vab, true);
