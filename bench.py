@@ -61,6 +61,32 @@ def _dist():
     return ws, rank, local
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Index-stream seed of replica `rank`: replicas draw independent streams."""
+    return base + 1000 * rank
+
+
+def batch_seed(rank: int, p: int) -> int:
+    """Seed of problem p of replica `rank` in the batched workload."""
+    return 1000 * (rank + 1) + p
+
+
+def job_ms(ms: float, ws: int, device) -> float:
+    """Whole-job time of a timed region: the maximum over ranks, one MAX
+    all-reduce of a scalar (the replicas' data paths have no collective)."""
+    if ws <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, samples_per_rank: int, ms: float) -> float:
+    """Whole-job throughput: every rank's samples over the slowest rank's time."""
+    return ws * samples_per_rank / (ms / 1e3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -234,7 +260,7 @@ def main():
     x = torch.zeros(pr.n, dtype=torch.float32, device="cuda")
     opts = dict(gram_dtype=args.gram, cluster=args.cluster, timing=1, seed_rank=rank)
     opts.pop("seed_rank")
-    seed = w["seed"] + 1000 * rank
+    seed = replica_seed(w["seed"], rank)
     plan = glm.glm_ca_plan(ds.h, s, b, w["eta"], w["lam"], T, glm.default_ca_opts(**opts))
 
     def step():
@@ -262,11 +288,8 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     ds.sync()
     kms, kl = glm.glm_kernel_times(ds.h)   # last step's per-kernel event times
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * T * b / (ms / 1e3)
+    ms = job_ms(ms, ws, "cuda")
+    value = job_value(ws, T * b, ms)
 
     # ---- roofline of the dominant kernel ------------------------------------
     peaks = _peaks()
@@ -410,7 +433,7 @@ def _batched(args, torch, synth, glm, rank):
     for sp in synth.batch_specs(P=cfg["P"], seed=cfg["data_seed"]):
         pr = synth.batch_problem(sp, seed=cfg["data_seed"])
         probs.append(dict(A=pr.A, y=pr.y, loss=sp["loss"], lam=sp["lam"], eta=cfg["eta"],
-                          iters=cfg["iters"], seed=1000 * (rank + 1) + sp["p"], b=cfg["b"],
+                          iters=cfg["iters"], seed=batch_seed(rank, sp["p"]), b=cfg["b"],
                           s=0))
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
