@@ -333,6 +333,12 @@ int make_tmap_2d_sw128(CUtensorMap *out, const void *base, int dt, uint64_t inne
                        uint64_t outer, uint64_t row_bytes, uint32_t box_inner,
                        uint32_t box_outer);
 
+// Bulk prefetch of [src, src + bytes) from global memory into L2 (src
+// 16-byte aligned, bytes a multiple of 16); no data reach shared memory.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Losses (paper Sec. 2.1): u = dL/dr and L itself
 // ---------------------------------------------------------------------------

@@ -156,23 +156,46 @@ k_chain_batch(const BatchItem *__restrict__ items, const int *__restrict__ order
       const TY *Yh = Y + (int64_t)h * sb * ldy;
       const float *lh = lab + (int64_t)h * sb;
       const float *Gh = G + (int64_t)h * gsz;
+      // the next outer step's rows and Gram blocks (contiguous in the round
+      // buffers) stream into L2 while this step runs: the round buffers are
+      // larger than L2, so without it every step would wait on DRAM
+      if (tid == 0 && h + 1 < nouter) {
+        prefetch_l2(Yh + (int64_t)sb * ldy, (uint32_t)((int64_t)sb * ldy * sizeof(TY)));
+        if (s >= 2) prefetch_l2(Gh + gsz, (uint32_t)(gsz * 4));
+      }
 
-      // ---- margins r = Y_h x (warp per row) ----
-      for (int r = warp; r < R; r += kBW) {
-        const TY *yr = Yh + (int64_t)r * ldy;
-        float acc = 0.f;
+      // ---- margins r = Y_h x (warp per row, four rows' loads in flight) ----
+      for (int r0 = warp; r0 < R; r0 += 4 * kBW) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int c0 = lane * 8; c0 < n; c0 += 256) {
-          float v[8];
-          Vec8<TY>::load(yr + c0, v);
+          float v[4][8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q * kBW;
+            if (r < R) {
+              Vec8<TY>::load(Yh + (int64_t)r * ldy + c0, v[q]);
+            } else {
+#pragma unroll
+              for (int k = 0; k < 8; ++k) v[q][k] = 0.f;
+            }
+          }
           const float4 x0 = *reinterpret_cast<const float4 *>(xs + c0);
           const float4 x1 = *reinterpret_cast<const float4 *>(xs + c0 + 4);
-          acc = fmaf(v[0], x0.x, acc); acc = fmaf(v[1], x0.y, acc);
-          acc = fmaf(v[2], x0.z, acc); acc = fmaf(v[3], x0.w, acc);
-          acc = fmaf(v[4], x1.x, acc); acc = fmaf(v[5], x1.y, acc);
-          acc = fmaf(v[6], x1.z, acc); acc = fmaf(v[7], x1.w, acc);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float a = acc[q];
+            a = fmaf(v[q][0], x0.x, a); a = fmaf(v[q][1], x0.y, a);
+            a = fmaf(v[q][2], x0.z, a); a = fmaf(v[q][3], x0.w, a);
+            a = fmaf(v[q][4], x1.x, a); a = fmaf(v[q][5], x1.y, a);
+            a = fmaf(v[q][6], x1.z, a); a = fmaf(v[q][7], x1.w, a);
+            acc[q] = a;
+          }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) rr[r] = (TR)acc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float t = warp_sum(acc[q]);
+          if (lane == 0 && r0 + q * kBW < R) rr[r0 + q * kBW] = (TR)t;
+        }
       }
       __syncthreads();
 
@@ -219,21 +242,29 @@ k_chain_batch(const BatchItem *__restrict__ items, const int *__restrict__ order
           float ae[8], cm[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) { ae[k] = 0.f; cm[k] = 0.f; }
-          for (int r = g; r < R; r += RG) {
-            float v[8];
-            Vec8<TY>::load(Yh + (int64_t)r * ldy + cg * 8, v);
-            const float w = (float)uh[r];
-            if (kahan) {
+          for (int r0 = g; r0 < R; r0 += 4 * RG) {
+            // four rows' loads in flight, then the sums in row order
+            float v[4][8];
 #pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const float yv = fmaf(v[k], w, -cm[k]);
-                const float t2 = ae[k] + yv;
-                cm[k] = (t2 - ae[k]) - yv;
-                ae[k] = t2;
+            for (int q = 0; q < 4; ++q)
+              if (r0 + q * RG < R) Vec8<TY>::load(Yh + (int64_t)(r0 + q * RG) * ldy + cg * 8, v[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int r = r0 + q * RG;
+              if (r >= R) break;
+              const float w = (float)uh[r];
+              if (kahan) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                  const float yv = fmaf(v[q][k], w, -cm[k]);
+                  const float t2 = ae[k] + yv;
+                  cm[k] = (t2 - ae[k]) - yv;
+                  ae[k] = t2;
+                }
+              } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) ae[k] = fmaf(v[q][k], w, ae[k]);
               }
-            } else {
-#pragma unroll
-              for (int k = 0; k < 8; ++k) ae[k] = fmaf(v[k], w, ae[k]);
             }
           }
 #pragma unroll
