@@ -1,0 +1,63 @@
+"""One-GPU analogue of the paper's recipe check (Sec. "Accuracy gap", the
+validation table there): the relative final-loss gap |L_C - L_A| / |L_A|
+between the BF16 recipe (BF16 storage with per-column scales, BF16 Gram and
+GEMV operands, FP32 accumulation; the recurrence as the library sets it) and
+the FP32 recipe, at (m, n) = (65,536, 4,096), b = 32, s in {16, 64}, H = 200
+outer iterations, three seeds, for logistic, least-squares and Poisson losses.
+The paper's cells (P = 16, its own synthetic data) are at most 3.3e-4 against
+a 0.5 % threshold; the bar here is the 1e-3 final-loss target.  The data are
+synthetic stand-ins with the paper's shape (rows of about unit norm); both
+losses are evaluated on the FP32 data.
+"""
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+M, N, B, H, LAM = 65536, 4096, 32, 200, 1e-4
+# step sizes: stable for unit-norm rows (logistic, least squares) and for the
+# exponential link at margins of about 0.5 (Poisson)
+CASES = {"logistic": (lambda: synth.logistic_planted(M, N, seed=31, lam=LAM), 0.5),
+         "lsq": (lambda: synth.lsq_planted(M, N, seed=32, noise=0.1, lam=LAM), 0.5),
+         "poisson": (lambda: synth.poisson_planted(M, N, seed=33, lam=LAM), 0.05)}
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2606_18463_gb300 import glm
+    glm.load()
+    return glm
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request, G):
+    make, eta = CASES[request.param]
+    pr = make()
+    A = torch.from_numpy(pr.A).cuda()
+    y = torch.from_numpy(pr.y).cuda()
+    ds_a = G.Dataset(A, y, pr.loss, "f32")
+    ds_c = G.Dataset(A, y, pr.loss, "bf16")
+    del A, y
+    yield request.param, eta, ds_a, ds_c
+    ds_a.close()
+    ds_c.close()
+
+
+@pytest.mark.parametrize("s", [16, 64])
+def test_recipe_c_vs_a_final_loss_gap(G, case, s):
+    name, eta, ds_a, ds_c = case
+    for seed in range(3):
+        xa = torch.zeros(N, dtype=torch.float32, device="cuda")
+        xc = torch.zeros(N, dtype=torch.float32, device="cuda")
+        ds_a.ca_sgd(xa, s, B, eta, LAM, H * s, seed, gram_dtype="f32")
+        ds_c.ca_sgd(xc, s, B, eta, LAM, H * s, seed, gram_dtype="bf16")
+        ds_a.sync()
+        ds_c.sync()
+        la = ds_a.loss_value(xa, LAM)
+        lc = ds_a.loss_value(xc, LAM)
+        gap = abs(lc - la) / abs(la)
+        print(f"recipe gap {name} s={s} seed={seed}: L_A={la:.8g} L_C={lc:.8g} gap={gap:.2e}")
+        assert gap <= 1e-3, (name, s, seed, la, lc, gap)
