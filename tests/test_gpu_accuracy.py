@@ -61,3 +61,37 @@ def test_recipe_c_vs_a_final_loss_gap(G, case, s):
         gap = abs(lc - la) / abs(la)
         print(f"recipe gap {name} s={s} seed={seed}: L_A={la:.8g} L_C={lc:.8g} gap={gap:.2e}")
         assert gap <= 1e-3, (name, s, seed, la, lc, gap)
+
+
+def test_long_horizon_gap(G):
+    # the paper's long-horizon stress run at one GPU: logistic, b = 32, s = 16,
+    # H = 320,000 outer iterations (5.12 M SGD steps), eta = 0.1; the two
+    # recipes resume in segments and their losses are compared at H = 20,000,
+    # 80,000 and 320,000 (the paper's mixed-precision recipes stay within
+    # 1.4e-6 of the FP32 one; the bar here is 1e-5)
+    pr = synth.logistic_planted(65536, 1024, seed=41, lam=0.0)
+    A = torch.from_numpy(pr.A).cuda()
+    y = torch.from_numpy(pr.y).cuda()
+    ds_a = G.Dataset(A, y, pr.loss, "f32")
+    ds_c = G.Dataset(A, y, pr.loss, "bf16")
+    del A, y
+    s, b, eta = 16, 32, 0.1
+    xa = torch.zeros(1024, dtype=torch.float32, device="cuda")
+    xc = torch.zeros(1024, dtype=torch.float32, device="cuda")
+    done = 0
+    try:
+        for h_end in (20000, 80000, 320000):
+            seg = h_end * s - done
+            ds_a.ca_sgd(xa, s, b, eta, 0.0, seg, 7, gram_dtype="f32", first_iter=done)
+            ds_c.ca_sgd(xc, s, b, eta, 0.0, seg, 7, gram_dtype="bf16", first_iter=done)
+            ds_a.sync()
+            ds_c.sync()
+            done = h_end * s
+            la = ds_a.loss_value(xa, 0.0)
+            lc = ds_a.loss_value(xc, 0.0)
+            gap = abs(lc - la) / abs(la)
+            print(f"long horizon H={h_end}: L_A={la:.8g} L_C={lc:.8g} gap={gap:.2e}")
+            assert gap <= 1e-5, (h_end, la, lc, gap)
+    finally:
+        ds_a.close()
+        ds_c.close()

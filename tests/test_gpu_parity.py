@@ -95,6 +95,8 @@ def test_ca_fp32_matches_oracle_c1(G, c1, cluster):
     (2000, 130, 12, 16, 200, synth.LOGISTIC, 1e-3),
     (3000, 64, 32, 8, 100, synth.LSQ, 0.0),
     (1024, 300, 9, 5, 47, synth.LSQ, 5e-3),
+    (4000, 18, 32, 8, 256, synth.LOGISTIC, 1e-4),   # SUSY-like width
+    (4000, 28, 32, 8, 256, synth.LSQ, 0.0),         # HIGGS-like width
 ])
 def test_ca_fp32_ragged_shapes(G, m, n, b, s, iters, loss, lam):
     pr = synth.ragged(m, n, seed=m + n, loss=loss, lam=lam)
