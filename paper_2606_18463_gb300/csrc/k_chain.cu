@@ -381,9 +381,8 @@ k_chain(const __grid_constant__ ChainArgs a) {
   // it).  Each copy completes transaction bytes on its slot's full barrier.
   const uint32_t ystep_bytes =
       (uint32_t)((int64_t)L.nbox * L.box_rows * nc * sizeof(TY) + round_up(sb, 4) * 4);
-  const int64_t nblk = gmode == G_BLOCK
-                           ? (int64_t)(a.nouter - 1) * (s - 1) + max(a.s_last - 1, 0)
-                           : 0;  // staged G block rows (j >= 1) of the launch
+  const int nblk = gmode == G_BLOCK ? (a.nouter - 1) * (s - 1) + max(a.s_last - 1, 0)
+                                   : 0;  // staged G block rows (j >= 1) of the launch
   auto issue_y = [&](int hh) {  // Y slice and labels of step hh
     if (ns == 0 || hh >= a.nouter) return;
     const int slot = hh % ns;
@@ -417,10 +416,10 @@ k_chain(const __grid_constant__ ChainArgs a) {
     }
     ++s_fills[kMaxSlots + slot];
   };
-  auto issue_gb = [&](int64_t kb) {  // G_BLOCK: block row kb of the launch (j >= 1 rows)
+  auto issue_gb = [&](int kb) {  // G_BLOCK: block row kb of the launch (j >= 1 rows)
     if (gmode != G_BLOCK || kb >= nblk) return;
-    const int hh = (int)(kb / (s - 1)), j = (int)(kb % (s - 1)) + 1;
-    const int slot = (int)(kb % ngs);
+    const int hh = kb / (s - 1), j = kb % (s - 1) + 1;
+    const int slot = kb % ngs;
     const int64_t ldj = gram_ld(j, b);
     const uint32_t bar = full_g0 + 8 * slot;
     mbar_arrive_expect_tx(bar, (uint32_t)(nown * ldj * 4));
@@ -446,10 +445,16 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const int groups = kCThreads / tpr; // row groups (kRows consecutive rows each)
   const int gi = tid / tpr, li = tid % tpr;
   const bool vsend_r = (b % 4 == 0) && (rpb % 4 == 0);            // 4 rows -> one v4
+  const int bi = (int)b;  // s b <= 8192: row indices fit 32 bits
+  // owner CTA and partial-margin slot of this group's first row in the first
+  // pass of the margin loop (the same every outer step)
+  const int own_a = ((gi * kRows) % bi) / rpb;
+  const int off_a = ((rank * s + (gi * kRows) / bi) * rpb + ((gi * kRows) % bi - own_a * rpb)) * 4;
   const int loss_kind = a.loss;
   unsigned *const flag = a.flag;
   const TY *Y = static_cast<const TY *>(a.Y);
-  int64_t kblk = 0;       // G block rows consumed (G_BLOCK mode)
+  int gslot = 0;          // G_BLOCK: slot of the next block row (kept as a counter:
+  uint32_t gpar = 0;      //   no division on the recurrence's path) and its phase parity
   bool abort = false;
   // update: 0 = folded in block by block by the workers, 1 = after the
   // recurrence by every consumer thread (row groups), 2 = after the
@@ -536,22 +541,29 @@ k_chain(const __grid_constant__ ChainArgs a) {
         for (int off = tpr / 2; off > 0; off >>= 1)
           acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], off);
       if (li == 0 && r0 < R) {
-        const int64_t j = r0 / b, l = r0 - j * b;
-        const int owner = (int)(l / rpb);
-        const int64_t ll = l - (int64_t)owner * rpb;
-        const uint32_t off4 = (uint32_t)((((int64_t)rank * s + j) * rpb + ll) * 4);
+        // owner CTA and slot of row r0 (the first pass's are precomputed:
+        // integer division by a run-time divisor is a long instruction sequence)
+        int owner, off4;
+        if (rb == 0) {
+          owner = own_a;
+          off4 = off_a;
+        } else {
+          const int r = (int)r0, j = r / bi, l = r - j * bi;
+          owner = l / rpb;
+          off4 = ((rank * s + j) * rpb + (l - owner * rpb)) * 4;
+        }
         if (vsend_r) {  // the 4 rows share block, owner and a 16-byte slot
-          st_async_v4(rem[owner] + off4, acc[0], acc[1], acc[2], acc[3], rem[16 + owner]);
+          st_async_v4(rem[owner] + (uint32_t)off4, acc[0], acc[1], acc[2], acc[3],
+                      rem[16 + owner]);
         } else {
 #pragma unroll
           for (int u = 0; u < kRows; ++u) {
-            const int64_t r = r0 + u;
+            const int r = (int)r0 + u;
             if (r < R) {
-              const int64_t ju = r / b, lu = r - ju * b;
-              const int ow = (int)(lu / rpb);
-              const int64_t lw = lu - (int64_t)ow * rpb;
-              st_async(rem[ow] + (uint32_t)((((int64_t)rank * s + ju) * rpb + lw) * 4), acc[u],
-                       rem[16 + ow]);
+              const int ju = r / bi, lu = r - ju * bi;
+              const int ow = lu / rpb;
+              st_async(rem[ow] + (uint32_t)(((rank * s + ju) * rpb + (lu - ow * rpb)) * 4),
+                       acc[u], rem[16 + ow]);
             }
           }
         }
@@ -609,8 +621,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
             if (lane == 0) {
               ok = wait_or_abort(bar_u + 8 * (j - 1), upar, vab, false);
               if (ok && gmode == G_BLOCK)
-                ok = wait_or_abort(full_g0 + 8 * (int)(kblk % ngs),
-                                   (uint32_t)((kblk / ngs) & 1), vab, false);
+                ok = wait_or_abort(full_g0 + 8 * gslot, gpar, vab, false);
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) {
               if (lane == 0) atomicOr(&s_abort, 1);
@@ -619,12 +630,12 @@ k_chain(const __grid_constant__ ChainArgs a) {
             // block j - 1 has landed everywhere: its G slot takes the block
             // row ngs further on
             if (!inc_e && tid == 0 && gmode == G_BLOCK && j >= 2)
-              issue_gb((int64_t)h * (s - 1) + (j - 2) + ngs);
+              issue_gb(h * (s - 1) + (j - 2) + ngs);
             if (gmode == G_STEP) {
               gofs = (h & 1) * L.gslot_floats + goff;
               goff += (int64_t)rpb * ldj;
             } else if (gmode == G_BLOCK) {
-              gofs = (kblk % ngs) * L.gslot_floats;
+              gofs = gslot * L.gslot_floats;
             } else {
               gofs = gram_off(j, b) + l0 * ldj;
             }
@@ -686,7 +697,10 @@ k_chain(const __grid_constant__ ChainArgs a) {
               }
             }
           }
-          if (gmode == G_BLOCK && j > 0) ++kblk;
+          if (gmode == G_BLOCK && j > 0 && ++gslot == ngs) {
+            gslot = 0;
+            gpar ^= 1u;
+          }
         }
       }
     } else if (wbase_t >= 0 && inc_e) {
@@ -720,7 +734,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
             break;
           }
           if (role == 1 && gmode == G_BLOCK && j >= 1)
-            issue_gb((int64_t)h * (s - 1) + (j - 1) + ngs);
+            issue_gb(h * (s - 1) + (j - 1) + ngs);
           if (role == 2 && j == 0 && h >= 1) issue_y(h + ns - 1);
           if (role == 3 && j == 0 && h >= 1) issue_gs(h + 1);
           if (!cols || !rows) continue;
@@ -765,7 +779,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
       if (!wait_or_abort(bar_u + 8 * (sh - 1), upar, vab, false)) {
         atomicOr(&s_abort, 1);
       } else if (gmode == G_BLOCK && sh >= 2) {  // the last block's G slot is free
-        issue_gb((int64_t)h * (s - 1) + (sh - 2) + ngs);
+        issue_gb(h * (s - 1) + (sh - 2) + ngs);
       }
     }
     csync();
