@@ -283,16 +283,16 @@ __device__ __forceinline__ void send4(uint32_t ra, const float (&w)[4], uint32_t
 }
 
 // Bounded wait that also gives up once another thread of the CTA has flagged
-// an abort; `nap` lets waiters off the critical path yield issue slots.
+// an abort.  Probes back to back, reading the clock and the flag on every
+// 32nd probe only (each extra read delays noticing the phase).
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
-                                              const volatile int *abort_flag, bool nap) {
+                                              const volatile int *abort_flag) {
   if (mbar_test_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_test_wait(bar, parity)) {
-    if (*abort_flag || clock64() - t0 > kWaitBudget) return false;
-    if (nap) __nanosleep(32);
+  for (unsigned k = 1;; ++k) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((k & 31) == 0 && (*abort_flag || clock64() - t0 > kWaitBudget)) return false;
   }
-  return true;
 }
 
 __device__ __forceinline__ void csync() { named_sync(1, kCThreads); }
@@ -619,9 +619,9 @@ k_chain(const __grid_constant__ ChainArgs a) {
             // lane 0 polls; the warp follows
             int ok = 1;
             if (lane == 0) {
-              ok = wait_or_abort(bar_u + 8 * (j - 1), upar, vab, false);
+              ok = wait_or_abort(bar_u + 8 * (j - 1), upar, vab);
               if (ok && gmode == G_BLOCK)
-                ok = wait_or_abort(full_g0 + 8 * gslot, gpar, vab, false);
+                ok = wait_or_abort(full_g0 + 8 * gslot, gpar, vab);
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) {
               if (lane == 0) atomicOr(&s_abort, 1);
@@ -670,7 +670,9 @@ k_chain(const __grid_constant__ ChainArgs a) {
               const TR yv = (TR)yown[j * rpb + rq];
               TR acc[4] = {0, 0, 0, 0};
               if (j > 0) {
-                if (gmode != G_NONE)
+                if (gmode != G_NONE && nq == 4)  // the common full group, fixed size
+                  rows_dot4<TR, true>(gbuf + gofs + q0 * ldj, ldj, 4, uh, jb, lane, acc);
+                else if (gmode != G_NONE)
                   rows_dot4<TR, true>(gbuf + gofs + q0 * ldj, ldj, nq, uh, jb, lane, acc);
                 else
                   rows_dot4<TR, false>(Gh + gofs + q0 * ldj, ldj, nq, uh, jb, lane, acc);
@@ -728,7 +730,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
       if (active) {
         for (int j = 0; j < sh; ++j) {
           int ok = 1;
-          if (lane == 0) ok = wait_or_abort(bar_u + 8 * j, upar, vab, true);
+          if (lane == 0) ok = wait_or_abort(bar_u + 8 * j, upar, vab);
           if (!__shfl_sync(act, ok, 0)) {
             atomicOr(&s_abort, 1);
             break;
@@ -776,7 +778,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
       }
     }
     if (!inc_e && tid == 0) {
-      if (!wait_or_abort(bar_u + 8 * (sh - 1), upar, vab, false)) {
+      if (!wait_or_abort(bar_u + 8 * (sh - 1), upar, vab)) {
         atomicOr(&s_abort, 1);
       } else if (gmode == G_BLOCK && sh >= 2) {  // the last block's G slot is free
         issue_gb(h * (s - 1) + (sh - 2) + ngs);
