@@ -569,36 +569,6 @@ k_chain(const __grid_constant__ ChainArgs a) {
         }
       }
     }
-    if (tid == 0 && !mbar_wait_bounded(bar_r, h & 1, kWaitBudget)) atomicOr(&s_abort, 1);
-    csync();
-    if (s_abort) { abort = true; break; }
-
-    // ---- C: own rows' margins (C-way shuffle trees, fixed order) and labels --
-    // entries across lanes (consecutive shared addresses), sources summed in a
-    // fixed order with four independent partial sums
-    for (int e = tid; e < sh * nown; e += kCThreads) {
-      const int j = e / nown, ll = e - j * nown;
-      const float *col = rrecv + (int64_t)j * rpb + ll;
-      const int64_t str = (int64_t)s * rpb;
-      TR p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-      int src = 0;
-      for (; src + 4 <= C; src += 4) {
-        p0 += (TR)col[(src + 0) * str];
-        p1 += (TR)col[(src + 1) * str];
-        p2 += (TR)col[(src + 2) * str];
-        p3 += (TR)col[(src + 3) * str];
-      }
-      for (; src < C; ++src) p0 += (TR)col[src * str];
-      rown[j * rpb + ll] = (p0 + p1) + (p2 + p3);
-      yown[j * rpb + ll] = labs[(int64_t)j * b + l0 + ll];
-    }
-    if (gmode == G_STEP && sh >= 2 && tid == 0) {
-      if (!mbar_wait_bounded(full_g0 + 8 * (h & 1), (uint32_t)((h >> 1) & 1), kWaitBudget))
-        atomicOr(&s_abort, 1);
-    }
-    csync();
-    if (s_abort) { abort = true; break; }
-
     // ---- D + E: recurrence on the row warps, update on the worker warps ----
     // Row warps run the serial loop over blocks.  Block j of every CTA lands
     // on this CTA's barrier bar_u[j]; a row warp waits on it before block
@@ -610,7 +580,45 @@ k_chain(const __grid_constant__ ChainArgs a) {
     if (rw >= 0) {
       const uint32_t ra_u = lane < C ? rem[32 + lane] : 0u;  // CTA lane's residual history
       const uint32_t rb_u = lane < C ? rem[48 + lane] : 0u;  // and its block barriers
-      {
+      // ---- C (per row warp): every CTA's partial margins of this warp's own
+      // rows, summed in a fixed order (four partial sums over the sources),
+      // and their labels; then the step's G rows (G_STEP).  No CTA barrier:
+      // only this warp reads them.
+      int okc = 1;
+      if (lane == 0) {
+        okc = wait_or_abort(bar_r, (uint32_t)(h & 1), vab);
+        if (okc && gmode == G_STEP && sh >= 2)
+          okc = wait_or_abort(full_g0 + 8 * (h & 1), (uint32_t)((h >> 1) & 1), vab);
+        if (!okc) atomicOr(&s_abort, 1);
+      }
+      okc = __shfl_sync(0xffffffffu, okc, 0);
+      if (okc) {
+        const int64_t str = (int64_t)s * rpb;
+        auto own_margin = [&](int j, int ll) {
+          const float *col = rrecv + (int64_t)j * rpb + ll;
+          TR p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+          int src = 0;
+          for (; src + 4 <= C; src += 4) {
+            p0 += (TR)col[(src + 0) * str];
+            p1 += (TR)col[(src + 1) * str];
+            p2 += (TR)col[(src + 2) * str];
+            p3 += (TR)col[(src + 3) * str];
+          }
+          for (; src < C; ++src) p0 += (TR)col[src * str];
+          rown[j * rpb + ll] = (p0 + p1) + (p2 + p3);
+          yown[j * rpb + ll] = labs[(int64_t)j * b + l0 + ll];
+        };
+        if constexpr (kF64) {
+          for (int rq = rw; rq < nown; rq += nrw)
+            for (int j = lane; j < sh; j += 32) own_margin(j, rq);
+        } else {
+          for (int q0 = 4 * rw; q0 < nown; q0 += 4 * nrw)
+            for (int e = lane; e < 4 * sh; e += 32)
+              if (q0 + (e & 3) < nown) own_margin(e >> 2, q0 + (e & 3));
+        }
+        __syncwarp();
+      }
+      if (okc) {
         int64_t goff = 0;  // floats into the G_STEP slot
         for (int j = 0; j < sh; ++j) {
           const int64_t ldj = gram_ld(j, b);
