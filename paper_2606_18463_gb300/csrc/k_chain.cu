@@ -663,7 +663,9 @@ k_chain(const __grid_constant__ ChainArgs a) {
                   corr += __shfl_xor_sync(0xffffffffu, corr, off);
               }
               const TR z = cj * rv - zj * corr;
-              const TR u = dloss<TR>(loss_kind, z, yv);
+              // the residual of the FP64 margin in FP32 (a single rounding; the
+              // correction sums, where errors compound with s, stay FP64)
+              const TR u = (TR)dloss<float>(loss_kind, (float)z, (float)yv);
               if (lane == 0 && (!isfinite(z) || !isfinite(u))) atomicOr(flag, FLAG_NONFINITE);
               if (lane < C)  // fan-out: lane d writes CTA d's copy of the residual
                 st_async(ra_u + (uint32_t)((jb + l0 + rq) * sizeof(TR)), u * ij, rb_u + 8 * j);
