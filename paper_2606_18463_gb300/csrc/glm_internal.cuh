@@ -208,16 +208,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-  return ok != 0;
-}
-
 // Non-suspending probe of a phase (a thread parked inside try_wait can take
 // microseconds to resume, which dominates latency-bound exchanges).
 __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
@@ -236,17 +226,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   if (mbar_test_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test_wait(bar, parity)) {
-    if (clock64() - t0 > budget) return false;
-  }
-  return true;
-}
-
-// Bounded wait that lets the hardware suspend the thread between probes; for
-// waiters off the critical path (a spinning warp would take issue slots).
-__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
-                                                long long budget) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > budget) return false;
   }
   return true;

@@ -13,20 +13,21 @@
 //        z_j = c^j r_j - alpha c^{j-1} sum_{i<j} G_{j,i} (c^{-i} u_i)
 //    and residuals, then sends c^{-j} u_j to every CTA.
 //
-// Warp roles in each CTA: 16 consumer warps do the arithmetic above and
-// synchronise among themselves only (named barrier 1).  During the
-// recurrence, the first few consumer warps each run the serial loop for own
-// rows dealt to them round-robin, while the others fold each block's
-// Y_j^T u_j into the update as soon as it lands.  Everything x-independent
-// is streamed into shared memory ahead of use -- the CTA's column slice of
-// the rows of Y and their labels (TMA 2D tiles and a bulk copy, `ns` outer
-// steps in flight) and the own rows of G_{j,<j} (bulk copies; a whole outer
-// step ahead when two steps fit, else one block row ahead) -- by one thread
-// that issues each copy once its slot is known to be free, behind full
-// mbarriers.  x-dependent values travel one
-// way: (vector) st.async into the owner's shared memory, completing
-// transaction bytes on the owner's mbarrier (one per block of residuals), so
-// an inner step costs one DSMEM latency and no cluster or CTA barrier.
+// Warp roles in each CTA (16 warps, CTA barrier = named barrier 1): during
+// the recurrence a few row warps each run the serial loop for their own rows
+// (FP32: groups of four rows on warps 0, 4, 8, 12; FP64: rows dealt round-
+// robin), summing those rows' partial margins themselves, while the other
+// warps fold each block's Y_j^T u_j into the update as soon as it lands.
+// Everything x-independent is streamed into shared memory ahead of use --
+// the CTA's column slice of the rows of Y and their labels (TMA 2D tiles and
+// a bulk copy, `ns` outer steps in flight) and the own rows of G_{j,<j}
+// (bulk copies: a whole outer step per slot when two steps fit, else one
+// block row per slot, up to four slots) -- each copy issued, behind a full
+// mbarrier, by lane 0 of one of three worker warps as soon as the slot it
+// reuses is known to be free.  x-dependent values travel one way: (vector)
+// st.async into the owner's shared memory, completing transaction bytes on
+// the owner's mbarrier (one per block of residuals), so an inner step costs
+// one DSMEM latency and no cluster or CTA barrier.
 // Every wait is bounded (FLAG_TIMEOUT; the kernel then drains its own copies
 // and unwinds without writing x).  Slices that do not fit are read from
 // global memory directly.
