@@ -298,7 +298,7 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
 
 __device__ __forceinline__ void csync() { named_sync(1, kCThreads); }
 
-template <typename TY, typename TR>
+template <typename TY, typename TR, bool kHot>
 __global__ void __launch_bounds__(kThreads, 1)
 k_chain(const __grid_constant__ ChainArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -309,7 +309,11 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const int s = a.s;
   const int64_t sb = (int64_t)s * b;
   const Layout L = make_layout(n, b, s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
-  const int nc = L.nc, rpb = L.rpb, ns = L.ns, gmode = L.gmode, ngs = L.ngs;
+  // kHot: the common layout fixed at compile time (a whole step of G per
+  // slot, staged Y, update folded in, fewer than 32 vectors per slice), so
+  // the once-per-step code carries none of the other branches
+  const int nc = L.nc, rpb = L.rpb, ns = L.ns;
+  const int gmode = kHot ? (int)G_STEP : L.gmode, ngs = kHot ? 2 : L.ngs;
   const int64_t col0 = (int64_t)rank * nc;
   const int64_t l0 = (int64_t)rank * rpb;
   const int nown = (int)max((int64_t)0, min((int64_t)rpb, b - l0));
@@ -460,7 +464,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
   // update: 0 = folded in block by block by the workers, 1 = after the
   // recurrence by every consumer thread (row groups), 2 = after the
   // recurrence, one thread per 8-column vector (slices wider than that)
-  const int emode = (nwt > 0 && V <= nwt) ? 0 : (V <= kCThreads ? 1 : 2);
+  const int emode = kHot ? 0 : ((nwt > 0 && V <= nwt) ? 0 : (V <= kCThreads ? 1 : 2));
   const bool inc_e = emode == 0;
   const int EG = emode == 0 ? nwt / V : (emode == 1 ? kCThreads / V : 1);  // row groups
   // copies are issued by worker thread 0 when workers fold the update in,
@@ -479,7 +483,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
       issue_y(h + ns - 1);
       issue_gs(h + 1);
     }
-    const bool staged = ns > 0;
+    const bool staged = kHot || ns > 0;
     const TY *Ys;          // row r of this CTA's slice at Ys + r * ystride
     int64_t ystride;
     const float *labs;
@@ -837,7 +841,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
           }
           csync();
         }
-        if (emode == 0 && V < 32) {
+        if (kHot || (emode == 0 && V < 32)) {
           // one partial per worker warp: a thread per column sums them in order
           if (tid < nc) {
             float S = 0.f, cS = 0.f;
@@ -976,6 +980,19 @@ bool cluster_rows_ok(int C, int64_t b) {
   return (int64_t)(C - 1) * rpb < b;
 }
 
+template <typename TY, typename TR, bool kHot>
+int launch_k(const ChainArgs &a, const Layout &L, int C, cudaStream_t st) {
+  auto kern = k_chain<TY, TR, kHot>;
+  GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)L.total));
+  if (C > 8)
+    GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = make_cfg(C, L.total, st, attr);
+  GLM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
+  return GLM_OK;
+}
+
 template <typename TY, typename TR>
 int launch_t(const ChainArgs &a0, cudaStream_t st) {
   ChainArgs a = a0;
@@ -989,20 +1006,15 @@ int launch_t(const ChainArgs &a0, cudaStream_t st) {
                          (uint64_t)a.nouter * a.s * a.b, (uint64_t)a.ldy * sizeof(TY),
                          (uint32_t)L.nc, (uint32_t)L.box_rows));
   }
-  auto kern = k_chain<TY, TR>;
-  GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)L.total));
-  if (C > 8)
-    GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = make_cfg(C, L.total, st, attr);
-  GLM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
-  return GLM_OK;
+  if constexpr (sizeof(TR) == 4) {
+    if (L.gmode == G_STEP && L.ns > 0 && L.nc / 8 < 32) return launch_k<TY, TR, true>(a, L, C, st);
+  }
+  return launch_k<TY, TR, false>(a, L, C, st);
 }
 
 template <typename TY, typename TR>
 int max_cluster_t(const ChainArgs &a) {
-  auto kern = k_chain<TY, TR>;
+  auto kern = k_chain<TY, TR, false>;
   for (int C = 16; C >= 1; C /= 2) {
     if (!cluster_rows_ok(C, a.b)) continue;
     const Layout L = make_layout(a.n, a.b, a.s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
