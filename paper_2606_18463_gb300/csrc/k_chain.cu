@@ -298,7 +298,7 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
 
 __device__ __forceinline__ void csync() { named_sync(1, kCThreads); }
 
-template <typename TY, typename TR, bool kHot>
+template <typename TY, typename TR, int kHot, int kV>
 __global__ void __launch_bounds__(kThreads, 1)
 k_chain(const __grid_constant__ ChainArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -309,11 +309,14 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const int s = a.s;
   const int64_t sb = (int64_t)s * b;
   const Layout L = make_layout(n, b, s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
-  // kHot: the common layout fixed at compile time (a whole step of G per
-  // slot, staged Y, update folded in, fewer than 32 vectors per slice), so
-  // the once-per-step code carries none of the other branches
+  // kHot != 0: a common layout fixed at compile time -- staged Y, update
+  // folded in, fewer than 32 vectors per slice, and G a whole step per slot
+  // (1) or one block row per slot (2); kV != 0 fixes the slice width too.
+  // The once-per-step code is bound by instruction fetch, so these instances
+  // carry none of the other layouts' branches.
   const int nc = L.nc, rpb = L.rpb, ns = L.ns;
-  const int gmode = kHot ? (int)G_STEP : L.gmode, ngs = kHot ? 2 : L.ngs;
+  const int gmode = kHot == 1 ? (int)G_STEP : (kHot == 2 ? (int)G_BLOCK : L.gmode);
+  const int ngs = kHot == 1 ? 2 : L.ngs;
   const int64_t col0 = (int64_t)rank * nc;
   const int64_t l0 = (int64_t)rank * rpb;
   const int nown = (int)max((int64_t)0, min((int64_t)rpb, b - l0));
@@ -444,7 +447,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
   }
 
   // ========================= consumer warps ==================================
-  const int V = nc / 8;               // 8-element vectors in the slice
+  const int V = kV ? kV : nc / 8;    // 8-element vectors in the slice
   const int tpr = V < 32 ? V : 32;    // threads per row in the margin
   const int vpt = V / tpr;            // vectors per thread per row
   const int groups = kCThreads / tpr; // row groups (kRows consecutive rows each)
@@ -980,9 +983,9 @@ bool cluster_rows_ok(int C, int64_t b) {
   return (int64_t)(C - 1) * rpb < b;
 }
 
-template <typename TY, typename TR, bool kHot>
+template <typename TY, typename TR, int kHot, int kV>
 int launch_k(const ChainArgs &a, const Layout &L, int C, cudaStream_t st) {
-  auto kern = k_chain<TY, TR, kHot>;
+  auto kern = k_chain<TY, TR, kHot, kV>;
   GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)L.total));
   if (C > 8)
@@ -1006,15 +1009,19 @@ int launch_t(const ChainArgs &a0, cudaStream_t st) {
                          (uint64_t)a.nouter * a.s * a.b, (uint64_t)a.ldy * sizeof(TY),
                          (uint32_t)L.nc, (uint32_t)L.box_rows));
   }
-  if constexpr (sizeof(TR) == 4) {
-    if (L.gmode == G_STEP && L.ns > 0 && L.nc / 8 < 32) return launch_k<TY, TR, true>(a, L, C, st);
+  if constexpr (sizeof(TR) == 4) {  // the compile-time instances (see k_chain)
+    if (L.ns > 0 && L.nc / 8 < 32) {
+      if (L.gmode == G_STEP)
+        return L.nc == 32 ? launch_k<TY, TR, 1, 4>(a, L, C, st) : launch_k<TY, TR, 1, 0>(a, L, C, st);
+      if (L.gmode == G_BLOCK) return launch_k<TY, TR, 2, 0>(a, L, C, st);
+    }
   }
-  return launch_k<TY, TR, false>(a, L, C, st);
+  return launch_k<TY, TR, 0, 0>(a, L, C, st);
 }
 
 template <typename TY, typename TR>
 int max_cluster_t(const ChainArgs &a) {
-  auto kern = k_chain<TY, TR, false>;
+  auto kern = k_chain<TY, TR, 0, 0>;
   for (int C = 16; C >= 1; C /= 2) {
     if (!cluster_rows_ok(C, a.b)) continue;
     const Layout L = make_layout(a.n, a.b, a.s, C, (int)sizeof(TR), (int)sizeof(TY), a.prefetch);
