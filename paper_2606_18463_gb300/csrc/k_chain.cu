@@ -302,7 +302,9 @@ template <typename TY, typename TR, int kHot, int kV>
 __global__ void __launch_bounds__(kThreads, 1)
 k_chain(const __grid_constant__ ChainArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
-  const int C = (int)cluster.num_blocks();
+  // kV == 4 instances are launched only for 16-CTA clusters with four own
+  // rows per block (the 2^20 x 512, b = 64 shape): those are constants too
+  const int C = kV == 4 ? 16 : (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = a.n, b = a.b;
@@ -314,7 +316,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
   // (1) or one block row per slot (2); kV != 0 fixes the slice width too.
   // The once-per-step code is bound by instruction fetch, so these instances
   // carry none of the other layouts' branches.
-  const int nc = L.nc, rpb = L.rpb, ns = L.ns;
+  const int nc = kV == 4 ? 32 : L.nc, rpb = kV == 4 ? 4 : L.rpb, ns = L.ns;
   const int gmode = kHot == 1 ? (int)G_STEP : (kHot == 2 ? (int)G_BLOCK : L.gmode);
   const int ngs = kHot == 1 ? 2 : L.ngs;
   const int64_t col0 = (int64_t)rank * nc;
@@ -1012,7 +1014,8 @@ int launch_t(const ChainArgs &a0, cudaStream_t st) {
   if constexpr (sizeof(TR) == 4) {  // the compile-time instances (see k_chain)
     if (L.ns > 0 && L.nc / 8 < 32) {
       if (L.gmode == G_STEP)
-        return L.nc == 32 ? launch_k<TY, TR, 1, 4>(a, L, C, st) : launch_k<TY, TR, 1, 0>(a, L, C, st);
+        return (L.nc == 32 && C == 16 && L.rpb == 4) ? launch_k<TY, TR, 1, 4>(a, L, C, st)
+                                                     : launch_k<TY, TR, 1, 0>(a, L, C, st);
       if (L.gmode == G_BLOCK) return launch_k<TY, TR, 2, 0>(a, L, C, st);
     }
   }
