@@ -120,8 +120,11 @@ typedef struct {
   int gemv_dtype;     /* u_r = u_g (margin and outer-gradient operands);
                          -1 (default) = gram_dtype, or the storage type when
                          gram_dtype is GLM_E4M3.                              */
-  int recurrence_f64; /* u_c = u_sigma: -1 (default) FP64 iff s >= 32,
-                         0 FP32, 1 FP64.                                      */
+  int recurrence_f64; /* u_c: -1 (default) FP64 iff s >= 32, 0 FP32, 1 FP64.
+                         In FP64 the correction sums and residual history
+                         are FP64 and each residual (u_sigma) is the FP32
+                         loss derivative of the FP64 margin; in FP32 the
+                         residual uses the fast exponential and division.  */
   int kahan;          /* 1 (default): Kahan-compensated FP32 Y^T u sums.      */
   int64_t first_iter; /* SGD-equivalent iteration the run starts at; draws
                          continue the counter-based stream from there, so a
