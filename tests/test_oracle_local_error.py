@@ -1,0 +1,341 @@
+"""Pins for the local error budget of one CA-SGD outer step (Theorem 1,
+Sec. 5.2) and for its rounding simulator (``oracle.local_error``).
+
+  * the p-bit rounding against numpy's float32 / float16 casts and the BF16
+    rounding, and directed rounding against numpy's nextafter;
+  * the exact outer step against the C oracle's SGD on the same index stream,
+    and its residual against the C oracle's loss derivative;
+  * the simulator without rounding against the exact step (CA-SGD equals SGD
+    in exact arithmetic);
+  * K_s against the terminating Neumann series and a 2 x 2 closed form; H_L,
+    T_g, T_r, T_G, T_c against element loops; s = 1 degenerations;
+  * each of the nine terms against the deviation the simulator shows with
+    that slot alone rounded: the term bounds it (within the first-order
+    factor 2 that stands for 1 + C_loc Omega), and under directed rounding it
+    is not looser than a fixed factor, so that a dropped or extra factor of
+    alpha, a missing term or a wrong reduction length fails;
+  * cases where every inequality behind a term is tight (one column, one or
+    two inner steps, least squares, the rounding model's extreme v (1 + u)
+    for every operation): the deviation equals the term to first order, so
+    a wrong factor or source quantity in any term fails;
+  * all slots rounded together within twice the sum;
+  * the Recipe C hypothesis figure printed in Sec. 5.3.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import local_error as le
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+U32, U16B, U16H = 2.0 ** -24, 2.0 ** -8, 2.0 ** -11
+
+
+def _problem(seed, loss, n=24, s=4, b=4, xnorm=2.0):
+    """Rows of norm in [1/2, 1] (Assumption 1), a start x of norm xnorm."""
+    rng = np.random.default_rng(seed)
+    sb = s * b
+    Y = rng.standard_normal((sb, n))
+    Y *= rng.uniform(0.5, 1.0, (sb, 1)) / np.linalg.norm(Y, axis=1, keepdims=True)
+    x = rng.standard_normal(n)
+    x *= xnorm / np.linalg.norm(x)
+    if loss == le.LOGISTIC:
+        y = np.where(rng.random(sb) < 0.5, -1.0, 1.0)
+    else:
+        y = Y @ (x + 0.3 * rng.standard_normal(n)) + 0.1 * rng.standard_normal(sb)
+    return Y, y, x
+
+
+# ----------------------------------------------------------------------------
+# Rounding model
+# ----------------------------------------------------------------------------
+def test_fl_matches_ieee_casts():
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(20000) * np.exp2(rng.integers(-10, 10, 20000))
+    assert np.array_equal(le.fl(v, 24), v.astype(np.float32).astype(np.float64))
+    h = v[(np.abs(v) >= 2.0 ** -14) & (np.abs(v) < 60000)]  # float16 normal range
+    assert np.array_equal(le.fl(h, 11), h.astype(np.float16).astype(np.float64))
+    f = v.astype(np.float32)
+    assert np.array_equal(le.fl(f.astype(np.float64), 8),
+                          oracle.round_bf16(f).astype(np.float64))
+    # halfway cases go to even
+    assert le.fl(np.float64(1 + 2.0 ** -24), 24) == 1.0
+    assert le.fl(np.float64(1 + 3 * 2.0 ** -24), 24) == 1 + 2.0 ** -22
+    assert le.fl(np.float64(0.0), 8) == 0.0
+
+
+def test_fl_up_is_next_float32_above():
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(20000)
+    f = v.astype(np.float32)
+    up = np.where(f.astype(np.float64) < v, np.nextafter(f, np.float32(np.inf)), f)
+    assert np.array_equal(le.fl(v, 24, "up"), up.astype(np.float64))
+    assert le.unit_roundoff(24, "up") == 2 * le.unit_roundoff(24)
+
+
+def test_gamma_domain():
+    assert le.gamma(0, 0.1) == 0.0
+    assert le.gamma(10, 1e-3) == pytest.approx(1e-2 / (1 - 1e-2), rel=1e-15)
+    with pytest.raises(ValueError):
+        le.gamma(256, 2.0 ** -8)
+    assert le.gamma_mixed(512, U16B, U32) == pytest.approx(2 * U16B + 512 * U32, rel=1e-4)
+
+
+# ----------------------------------------------------------------------------
+# The exact outer step and the simulator
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("loss", [oracle.LOGISTIC, oracle.LSQ])
+def test_exact_step_is_the_c_oracle_sgd(loss):
+    import synth
+    m, n, s, b, eta, seed, k0 = 4096, 32, 6, 8, 0.5, 3, 40
+    pr = (synth.logistic_planted(m, n, seed=2) if loss == oracle.LOGISTIC
+          else synth.lsq_planted(m, n, seed=2, noise=0.1))
+    x0 = oracle.sgd(pr.A, pr.y, loss, b, eta, 0.0, k0, seed).astype(np.float32).astype(float)
+    idx = oracle.sample_indices(seed, 0, k0 * b, s * b, m)
+    Y = pr.A[idx].astype(np.float64)
+    yI = pr.y[idx].astype(np.float64)
+    z, d, xs = le.exact_step(Y, yI, x0, loss, eta, s, b)
+    ref = oracle.sgd(pr.A, pr.y, loss, b, eta, 0.0, s, seed, x0=x0, first_iter=k0)
+    assert np.allclose(xs[-1], ref, rtol=0, atol=1e-13 * np.linalg.norm(ref))
+    # residual = minus the C oracle's loss derivative at the exact margins
+    dl = np.array([oracle.dloss(loss, zi, yi) for zi, yi in zip(z, yI)])
+    assert np.allclose(d, -dl, rtol=1e-14, atol=1e-15)
+    # the inner iterates reproduce the margins
+    for j in range(s):
+        assert np.allclose(z[j * b:(j + 1) * b], Y[j * b:(j + 1) * b] @ xs[j], atol=1e-14)
+
+
+@pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
+@pytest.mark.parametrize("s,b", [(1, 4), (4, 4), (7, 3)])
+def test_simulator_without_rounding_is_exact(loss, s, b):
+    Y, y, x = _problem(5, loss, n=20, s=s, b=b)
+    _, _, xs = le.exact_step(Y, y, x, loss, 0.5, s, b)
+    xh = le.simulate_step(Y, y, x, loss, 0.5, s, b)
+    assert np.allclose(xh, xs[-1], rtol=0, atol=1e-13)
+    with pytest.raises(ValueError):
+        le.simulate_step(Y, y, x, loss, 0.5, s, b, {"q": 8})
+
+
+# ----------------------------------------------------------------------------
+# Source quantities and K_s
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
+def test_source_quantities_by_element_loops(loss):
+    s, b, n, eta = 4, 3, 10, 0.5
+    Y, y, x = _problem(7, loss, n=n, s=s, b=b)
+    ev = le.local_error(Y, y, x, loss, eta, s, b)
+    sb = s * b
+    d = ev["d"]
+    H = np.zeros((sb, sb))
+    for p in range(sb):
+        for q in range(sb):
+            if p // b > q // b:
+                H[p, q] = sum(abs(Y[p, k]) * abs(Y[q, k]) for k in range(n))
+    assert ev["norm_H_L"] == pytest.approx(np.linalg.svd(H, compute_uv=False)[0], rel=1e-12)
+    Tg = math.sqrt(sum(sum(abs(Y[p, k]) * abs(d[p]) for p in range(sb)) ** 2 for k in range(n)))
+    Tr = math.sqrt(sum(sum(abs(Y[p, k]) * abs(x[k]) for k in range(n)) ** 2 for p in range(sb)))
+    TG = math.sqrt(sum(sum(H[p, q] * abs(d[q]) for q in range(sb)) ** 2 for p in range(sb)))
+    Tc2 = 0.0
+    for j in range(1, s):
+        gf = math.sqrt(sum((Y[p] @ Y[q]) ** 2 for p in range(j * b, (j + 1) * b)
+                           for q in range(j * b)))
+        dn = math.sqrt(sum(d[q] ** 2 for q in range(j * b)))
+        Tc2 += (j * b * gf * dn) ** 2
+    assert ev["T_g"] == pytest.approx(Tg, rel=1e-12)
+    assert ev["T_r"] == pytest.approx(Tr, rel=1e-12)
+    assert ev["T_G"] == pytest.approx(TG, rel=1e-12)
+    assert ev["T_c"] == pytest.approx(math.sqrt(Tc2), rel=1e-12)
+    # K_s from the terminating Neumann series of the nilpotent L alpha |G_L|
+    blk = np.arange(sb) // b
+    N = ev["L_sigma"] * (eta / b) * np.where(blk[:, None] > blk[None, :], np.abs(Y @ Y.T), 0)
+    S, P = np.eye(sb), np.eye(sb)
+    for _ in range(s - 1):
+        P = P @ N
+        S = S + P
+    assert np.allclose(np.linalg.matrix_power(N, s), 0.0, atol=1e-300)
+    assert ev["K_s"] == pytest.approx(np.linalg.svd(S, compute_uv=False)[0], rel=1e-12)
+
+
+@pytest.mark.parametrize("loss,L", [(le.LOGISTIC, 0.25), (le.LSQ, 1.0)])
+def test_K_s_two_by_two_closed_form(loss, L):
+    # two single-row steps on the same unit row: |G_L| = [[0, 0], [1, 0]], so
+    # K_2 = ||[[1, 0], [a, 1]]||_2 = (a + sqrt(a^2 + 4)) / 2 with a = L eta
+    eta = 0.75
+    Y = np.array([[0.6, 0.8], [0.6, 0.8]])
+    ev = le.local_error(Y, np.array([1.0, -1.0]), np.array([0.3, -0.2]), loss, eta, 2, 1)
+    a = L * eta
+    assert ev["K_s"] == pytest.approx((a + math.sqrt(a * a + 4)) / 2, rel=1e-14)
+    assert ev["norm_H_L"] == pytest.approx(1.0, rel=1e-14)
+    assert ev["norm_Y"] == pytest.approx(math.sqrt(2), rel=1e-14)
+
+
+def test_single_inner_step_degenerates():
+    Y, y, x = _problem(9, le.LOGISTIC, n=16, s=1, b=6)
+    ev = le.local_error(Y, y, x, le.LOGISTIC, 0.5, 1, 6, u_A=U16B, u_c=U32)
+    assert ev["K_s"] == 1.0 and ev["T_G"] == 0.0 and ev["T_c"] == 0.0 and ev["norm_H_L"] == 0.0
+    assert ev["tau_G"] == 0.0
+    with pytest.raises(ValueError):
+        le.local_error(Y, y, x, 2, 0.5, 1, 6)  # Poisson: outside the theorem
+    with pytest.raises(ValueError):
+        le.local_error(Y[:5], y[:5], x, le.LOGISTIC, 0.5, 1, 6)
+
+
+# ----------------------------------------------------------------------------
+# Each term against the simulator
+# ----------------------------------------------------------------------------
+KEY = dict(A="E_A", r="E_r", G="E_G", c="E_c", sigma="E_sigma", g="E_g", x="E_x")
+# smallest deviation / term under directed rounding seen over seeds 0..19 of
+# _problem is 3.2 times or more above these floors (both losses, p = 8 and 11)
+FLOOR = dict(A=1e-2, r=5e-3, G=1e-3, c=5e-3, sigma=2e-3, g=1e-2, x=5e-2)
+
+
+def _slot_args(slot, u, n, sb):
+    return {"A": dict(u_A=u), "r": dict(gamma_r=le.gamma(n, u)),
+            "G": dict(gamma_G=le.gamma(n, u)), "c": dict(u_c=u),
+            "sigma": dict(u_sigma=u), "g": dict(gamma_g=le.gamma(sb, u)),
+            "x": dict(u_x=u)}[slot]
+
+
+@pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
+@pytest.mark.parametrize("mode", ["nearest", "up"])
+@pytest.mark.parametrize("p", [8, 11])
+def test_each_term_bounds_its_slot(loss, mode, p):
+    n, s, b, eta = 24, 4, 4, 0.5
+    u = le.unit_roundoff(p, mode)
+    for seed in range(8):
+        Y, y, x = _problem(seed, loss, n, s, b)
+        for slot in le.SLOTS:
+            ev = le.local_error(Y, y, x, loss, eta, s, b, **_slot_args(slot, u, n, s * b))
+            assert ev["omega"] <= 0.5 and ev["tau_G"] <= 0.5
+            dev = np.linalg.norm(le.simulate_step(Y, y, x, loss, eta, s, b, {slot: p}, mode)
+                                 - ev["x_s"])
+            E = ev[KEY[slot]]
+            assert 0 < dev <= 2 * E, (slot, seed, dev, E)
+            if mode == "up":
+                assert dev >= FLOOR[slot] * E, (slot, seed, dev / E)
+            # the other terms vanish with their slots exact
+            assert ev["sum"] == pytest.approx(E, rel=1e-15)
+
+
+TIGHT_P = 20  # u = 2^-20: second-order effects near 1e-6 of the first-order ones
+
+
+def _tight(slot, Y, y, x, eta, s, b, **factors):
+    Y, y, x = (np.array(v, dtype=float) for v in (Y, y, x))
+    ev = le.local_error(Y, y, x, le.LSQ, eta, s, b, **factors)
+    dev = np.linalg.norm(le.simulate_step(Y, y, x, le.LSQ, eta, s, b, {slot: TIGHT_P}, "model")
+                         - ev["x_s"])
+    return dev / ev["sum"]
+
+
+def test_terms_are_attained_in_tight_cases():
+    u = le.unit_roundoff(TIGHT_P, "model")
+    g1 = le.gamma(1, u)
+    # one row, one column, one step: K_s = 1, ||Y||_2 = |a|, every norm is an
+    # absolute value and the least-squares residual has slope exactly -1
+    one = dict(Y=[[0.8]], y=[2.0], x=[0.5], eta=0.5, s=1, b=1)
+    assert _tight("r", **one, gamma_r=g1) == pytest.approx(1, abs=1e-4)
+    assert _tight("g", **one, gamma_g=g1) == pytest.approx(1, abs=1e-4)
+    # x^(s) and alpha Y^T d of one sign: both roundings of the update add up
+    assert _tight("x", **one, u_x=u) == pytest.approx(1, abs=1e-4)
+    assert _tight("x", **dict(one, x=[0.0]), u_x=u) == pytest.approx(1, abs=1e-4)
+    # d < 0 with a x > 0: the margin and the gradient effects of the stored
+    # row add up (T_r and T_g parts of E_A)
+    assert _tight("A", **dict(one, y=[-1.0]), u_A=u) == pytest.approx(1, abs=1e-4)
+    # four equal unit rows (||Y||_2 = 2 = sqrt(sb)), |d| = max|y| + R = D_delta
+    assert _tight("sigma", [[1.0]] * 4, [0.5] * 4, [-1.0], 0.25, 1, 4,
+                  u_sigma=u) == pytest.approx(1, abs=1e-4)
+    # two steps, x = 0, a tiny first row: ||Y||_2 K_s -> |a_1| and the
+    # correction error 3 u alpha G_10 d_0 (product, alpha scaling, sum) meets
+    # 2 alpha T_G + alpha T_c, the Gram error alpha^2 gamma_1 T_G
+    two = dict(Y=[[1e-3], [1.0]], y=[1.0, 0.3], x=[0.0], eta=0.125, s=2, b=1)
+    assert _tight("G", **two, gamma_G=g1) == pytest.approx(1, abs=1e-4)
+    assert _tight("c", **two, u_c=u) == pytest.approx(1, abs=1e-4)
+    # a zero first row: only the rounding of r_1 + 0 is left, the u_c T_r part
+    assert _tight("c", [[0.0], [0.8]], [1.0, 0.3], [0.5], 0.125, 2, 1,
+                  u_c=u) == pytest.approx(1, abs=1e-4)
+    # large alpha with the second residual zero: the stored rows' Gram effect
+    # 2 alpha^2 T_G outweighs the gradient's alpha T_g and they add up, within
+    # the looseness of ||Y||_2 K_s (0.93 of the term here)
+    r = _tight("A", [[1e-3], [1.0]], [1.0, 16.0 * 1e-3], [0.0], 16.0, 2, 1, u_A=u)
+    assert 0.9 <= r <= 1.0, r
+
+
+def test_logistic_slope_is_attained_near_zero_margin():
+    # the logistic residual's slope sigma (1 - sigma) reaches L_sigma = 1/4 at
+    # margin 0: a margin of 1e-3 makes the margin term tight
+    u = le.unit_roundoff(TIGHT_P, "model")
+    Y, y, x = np.array([[1.0]]), np.array([1.0]), np.array([1e-3])
+    ev = le.local_error(Y, y, x, le.LOGISTIC, 0.5, 1, 1, gamma_r=le.gamma(1, u))
+    dev = np.linalg.norm(le.simulate_step(Y, y, x, le.LOGISTIC, 0.5, 1, 1, {"r": TIGHT_P},
+                                          "model") - ev["x_s"])
+    assert dev / ev["E_r"] == pytest.approx(1, abs=1e-4)
+
+
+@pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
+def test_first_order_terms_bound_the_rounding_model_extreme(loss):
+    # with u = 2^-20 the second-order remainder is negligible: each term alone
+    # bounds its slot's deviation with no slack (largest ratio seen 0.99, for
+    # the update slot)
+    u = le.unit_roundoff(TIGHT_P, "model")
+    for seed in range(10):
+        for n, s, b in ((24, 4, 4), (8, 6, 2), (40, 3, 8)):
+            Y, y, x = _problem(200 + seed, loss, n, s, b)
+            for slot in le.SLOTS:
+                ev = le.local_error(Y, y, x, loss, 0.5, s, b, **_slot_args(slot, u, n, s * b))
+                dev = np.linalg.norm(le.simulate_step(Y, y, x, loss, 0.5, s, b,
+                                                      {slot: TIGHT_P}, "model") - ev["x_s"])
+                assert dev <= (1 + 1e-3) * ev[KEY[slot]], (slot, seed, n, s, b)
+
+
+@pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
+def test_all_slots_together(loss):
+    # BF16-like storage, kernels, residual and weights; FP32-like recurrence
+    n, s, b, eta = 32, 6, 4, 0.5
+    prec = dict(A=8, r=8, G=8, c=24, sigma=8, g=8, x=8)
+    for seed in range(6):
+        Y, y, x = _problem(100 + seed, loss, n, s, b)
+        u8 = le.unit_roundoff(8)
+        ev = le.local_error(Y, y, x, loss, eta, s, b, u_A=u8, gamma_r=le.gamma(n, u8),
+                            gamma_G=le.gamma(n, u8), u_c=U32, u_sigma=u8,
+                            gamma_g=le.gamma(s * b, u8), u_x=u8)
+        assert ev["Omega"] <= 0.5
+        dev = np.linalg.norm(le.simulate_step(Y, y, x, loss, eta, s, b, prec) - ev["x_s"])
+        assert 0 < dev <= 2 * ev["sum"], (seed, dev, ev["sum"])
+
+
+# ----------------------------------------------------------------------------
+# The printed Recipe C figure
+# ----------------------------------------------------------------------------
+def _golden():
+    vals = {}
+    with open(os.path.join(GOLDEN, "local_error_recipe_c.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_recipe_c_hypothesis_figure():
+    g = _golden()
+    b, s, P, n_loc, eta = int(g["b"]), int(g["s"]), int(g["P"]), int(g["n_loc"]), g["eta"]
+    sb, n = s * b, P * n_loc
+    rng = np.random.default_rng(11)
+    Y = rng.standard_normal((sb, n))
+    Y /= np.linalg.norm(Y, axis=1, keepdims=True)  # Assumption 1 at the boundary
+    y = np.where(rng.random(sb) < 0.5, -1.0, 1.0)
+    CP = 2.4 * P
+    ev = le.local_error(Y, y, np.zeros(n), le.LOGISTIC, eta, s, b,
+                        u_A=U16B, gamma_r=le.gamma_mixed(n_loc, U16B, U32),
+                        gamma_G=le.gamma_mixed(n_loc, U16B, U32), u_c=U32, u_sigma=U32,
+                        gamma_g=le.gamma_mixed(sb, U16B, U32), u_x=U32,
+                        cP_u_AR_r=CP * U16B, cP_u_AR_G=CP * U32)
+    assert CP * U16B == pytest.approx(g["CP_u16"], abs=5e-3)
+    assert ev["Omega"] <= g["Omega_C_max"]
+    # the margin all-reduce dominates: the Gram figure tau_G stays below it
+    assert ev["Omega"] == ev["omega"] == CP * U16B
+    assert ev["tau_G"] < ev["omega"]
