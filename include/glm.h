@@ -179,6 +179,31 @@ int glm_sgd_run_ex(glm_handle h, int64_t b, float eta, float lambda,
                    const glm_ca_opts *opts);
 
 /*
+ * End-to-end low-precision mini-batch SGD: the paper's end-to-end BF16 and
+ * FP16 baselines (Recipes I and H of the precision-symbol table, Sec. 5.3,
+ * run as plain mini-batch SGD as in the end-to-end check of Sec. 7,
+ * "Accuracy gap").  The state type T is the handle's storage type (GLM_BF16
+ * or GLM_F16).  Per iteration t it draws b rows from the same index stream as
+ * glm_sgd_run (draws (first_iter + t) b .. + b - 1, stream id 0), then
+ *     z = T(Y x),  u = T(dL/dr(z, y_I)),  g = T(Y^T u),
+ *     x <- T(c x - alpha g),   alpha = eta / b, c = 1 - eta lambda,
+ * where T(.) rounds to nearest even once.  The residual and the update are
+ * evaluated in FP32; the inner products accumulate in FP32 (accumulate =
+ * GLM_F32) or, with FP16 storage only, in FP16 by fused multiply-adds
+ * (accumulate = GLM_F16, Recipe H's FP16 accumulation).  Power-of-two
+ * column scales of the storage fold into the weights exactly.
+ * x: device FP32[n], read as x_0 (each entry rounded to T first) and
+ * overwritten with x_T (values of T).  iters >= 0, 1 <= b <= 1024,
+ * 0 <= eta*lambda < 1, first_iter >= 0; n up to about 27,000
+ * (GLM_EUNSUPPORTED beyond the on-chip state).  Runs on one SM (a baseline,
+ * not a fast path), allocates nothing and returns once the work is enqueued
+ * on the handle's stream; non-finite values raise the handle's flag.
+ */
+int glm_sgd_lowp_run(glm_handle h, int64_t b, float eta, float lambda,
+                     int64_t iters, uint64_t seed, float *x, int accumulate,
+                     int64_t first_iter);
+
+/*
  * CA-SGD (paper Algorithm 1, with the ridge decay c).  Each outer iteration
  * draws s*b indices, gathers Y (s b x n), forms r = Y x and the strictly
  * block-lower Gram blocks G_{j,i} = Y_j Y_i^T (i < j), runs

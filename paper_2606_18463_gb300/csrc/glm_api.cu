@@ -642,6 +642,46 @@ int glm_ca_sgd_run(glm_handle h, int s, int64_t b, float eta, float lambda, int6
   return glm_ca_sgd_run_ex(h, s, b, eta, lambda, iters, seed, x, nullptr);
 }
 
+int glm_sgd_lowp_run(glm_handle hh, int64_t b, float eta, float lambda, int64_t iters,
+                     uint64_t seed, float *x, int accumulate, int64_t first_iter) {
+  g_last_error.clear();
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h) return set_error(GLM_EINVAL, "null handle");
+  if (!x) return set_error(GLM_EINVAL, "x is NULL");
+  if (h->dtype != GLM_BF16 && h->dtype != GLM_F16)
+    return set_error(GLM_EINVAL, "low-precision SGD needs BF16 or FP16 storage");
+  if (accumulate != GLM_F32 && !(accumulate == GLM_F16 && h->dtype == GLM_F16))
+    return set_error(GLM_EINVAL, "accumulate must be GLM_F32, or GLM_F16 with FP16 storage");
+  if (b < 1 || b > 1024) return set_error(GLM_EINVAL, "b must be in [1, 1024]");
+  if (iters < 0) return set_error(GLM_EINVAL, "iters must be >= 0");
+  if (first_iter < 0) return set_error(GLM_EINVAL, "first_iter must be >= 0");
+  if (!(eta > 0.f) || !isfinite(eta)) return set_error(GLM_EINVAL, "eta must be finite and > 0");
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return set_error(GLM_EINVAL, "lambda must be >= 0");
+  const double c = 1.0 - (double)eta * (double)lambda;
+  if (!(c > 0.0)) return set_error(GLM_EINVAL, "eta * lambda must be < 1");
+  if (!lowp_fits(h->n, (int)b))
+    return set_error(GLM_EUNSUPPORTED, "n too large for the on-chip low-precision state");
+  if (iters == 0) return GLM_OK;
+  LowpArgs a = {};
+  a.A = h->A;
+  a.lda = h->lda;
+  a.colscale = h->colscale;
+  a.y = h->y;
+  a.m = h->m;
+  a.n = h->n;
+  a.b = (int)b;
+  a.loss = h->loss;
+  a.seed = seed;
+  a.problem = 0;
+  a.q0 = (uint64_t)first_iter * (uint64_t)b;
+  a.iters = iters;
+  a.alpha = (float)((double)eta / (double)b);
+  a.c = (float)c;
+  a.x = x;
+  a.flag = h->dflag;
+  return launch_sgd_lowp(a, h->dtype, accumulate == GLM_F16 ? 1 : 0, h->stream);
+}
+
 int glm_ca_plan(glm_handle hh, int s, int64_t b, float eta, float lambda, int64_t iters,
                 const glm_ca_opts *opts, glm_run_plan *out) {
   g_last_error.clear();

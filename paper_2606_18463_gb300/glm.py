@@ -34,7 +34,7 @@ DTYPES = {"f32": GLM_F32, "bf16": GLM_BF16, "f16": GLM_F16, "tf32": GLM_TF32,
 EXPORTED = [
     "glm_last_error", "glm_version", "glm_create_opts_default", "glm_create",
     "glm_create_ex", "glm_destroy", "glm_shape", "glm_stream", "glm_sync",
-    "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_ca_sgd_run",
+    "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_sgd_lowp_run", "glm_ca_sgd_run",
     "glm_ca_sgd_run_ex", "glm_ca_plan", "glm_kernel_times", "glm_loss",
     "glm_sample_indices", "glm_sample_indices_noalloc", "glm_gram_lower",
     "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
@@ -114,6 +114,7 @@ def load():
             "glm_sgd_run": ([vp, i64, f32, f32, i64, u64, vp], i32),
             "glm_sgd_run_ex": ([vp, i64, f32, f32, i64, u64, vp,
                                 ctypes.POINTER(glm_ca_opts)], i32),
+            "glm_sgd_lowp_run": ([vp, i64, f32, f32, i64, u64, vp, i32, i64], i32),
             "glm_ca_sgd_run": ([vp, i32, i64, f32, f32, i64, u64, vp], i32),
             "glm_ca_sgd_run_ex": ([vp, i32, i64, f32, f32, i64, u64, vp,
                                    ctypes.POINTER(glm_ca_opts)], i32),
@@ -209,6 +210,11 @@ def glm_sgd_run(h, b, eta, lam, iters, seed, x, opts=None) -> None:
         _check(load().glm_sgd_run(h, b, eta, lam, iters, seed, _ptr(x)))
     else:
         _check(load().glm_sgd_run_ex(h, b, eta, lam, iters, seed, _ptr(x), ctypes.byref(opts)))
+
+
+def glm_sgd_lowp_run(h, b, eta, lam, iters, seed, x, accumulate="f32", first_iter=0) -> None:
+    acc = DTYPES[accumulate] if isinstance(accumulate, str) else accumulate
+    _check(load().glm_sgd_lowp_run(h, b, eta, lam, iters, seed, _ptr(x), acc, first_iter))
 
 
 def glm_ca_sgd_run(h, s, b, eta, lam, iters, seed, x, opts=None) -> None:
@@ -313,6 +319,9 @@ class Dataset:
     def sgd(self, x, b, eta, lam, iters, seed, **opts):
         glm_sgd_run(self.h, b, eta, lam, iters, seed, x,
                     default_ca_opts(**opts) if opts else None)
+
+    def sgd_lowp(self, x, b, eta, lam, iters, seed, accumulate="f32", first_iter=0):
+        glm_sgd_lowp_run(self.h, b, eta, lam, iters, seed, x, accumulate, first_iter)
 
     def ca_sgd(self, x, s, b, eta, lam, iters, seed, **opts):
         glm_ca_sgd_run(self.h, s, b, eta, lam, iters, seed, x,
