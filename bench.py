@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -105,17 +106,21 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = None
 
     def start(self):
+        self.p = None
+        fd, self.path = tempfile.mkstemp(prefix=f".glm_clocks_rank{self.index}_", suffix=".csv",
+                                         dir=ROOT)
+        self.f = os.fdopen(fd, "w")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
                                        f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                        "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            self.f.close()
+            os.unlink(self.path)
 
     def stop(self):
         if self.p is None:
@@ -126,9 +131,12 @@ class Clocks:
         except Exception:
             self.p.kill()
         self.f.close()
+        with open(self.path) as f:
+            lines = f.readlines()
+        os.unlink(self.path)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
