@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "glm_internal.cuh"
+#include "glm_lowp.cuh"
 
 namespace glm {
 

@@ -92,7 +92,9 @@ struct Batch {
 
 namespace {
 
-int64_t ld_for(int dt, int64_t n) { return round_up(n, 64); }
+// row pitch of the gathered operand rows: 64 elements for every batched
+// operand type (the FP8 Gram is not offered in batches)
+int64_t ld_for(int64_t n) { return round_up(n, 64); }
 
 // Plan a run of the problems `sel` (indices) with their s, iterating
 // `iters[k]` SGD-equivalent iterations each.
@@ -104,7 +106,7 @@ void make_plan(const Batch &B, const std::vector<int> &sel, const std::vector<in
   for (size_t k = 0; k < sel.size(); ++k) {
     const Prob &p = B.pr[sel[k]];
     const int64_t sb = (int64_t)p.s * p.b;
-    per_outer += sb * (ld_for(B.gdt, p.n) * eb + 4) + gram_size(p.s, p.b) * 4;
+    per_outer += sb * (ld_for(p.n) * eb + 4) + gram_size(p.s, p.b) * 4;
     hmax = std::max<int64_t>(hmax, (iters[k] + p.s - 1) / p.s);
     pl.max_n = std::max<int>(pl.max_n, (int)p.n);
     pl.max_sb = std::max<int>(pl.max_sb, (int)sb);
@@ -131,7 +133,7 @@ void make_plan(const Batch &B, const std::vector<int> &sel, const std::vector<in
     for (auto &kv : grp) {
       const int s = std::get<0>(kv.first);
       const int64_t b = std::get<1>(kv.first), n = std::get<2>(kv.first);
-      const int64_t sb = s * b, ld = ld_for(B.gdt, n);
+      const int64_t sb = s * b, ld = ld_for(n);
       Group g{s, b, n, ld, 0, reinterpret_cast<void *>(yoff), reinterpret_cast<float *>(goff)};
       for (auto &e : kv.second) {
         const int k = e.first;

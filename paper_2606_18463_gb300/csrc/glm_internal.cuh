@@ -484,22 +484,6 @@ int launch_gather_batch(const BatchItem *items, int nitems, int64_t max_rows, cu
 int launch_chain_batch(const BatchItem *items, const int *order, int nitems, int *queue,
                        int y_dt, int rec64, int max_n, int max_sb, int max_s, cudaStream_t st);
 
-// End-to-end low-precision mini-batch SGD (k_sgd_lowp.cu): `iters` steps of
-// b rows each, draws q0, q0 + 1, ... of the (seed, problem) stream; x is the
-// FP32[n] iterate, read at the start (rounded to the storage type) and
-// written at the end.
-struct LowpArgs {
-  const void *A; int64_t lda; const float *colscale; const float *y;
-  int64_t m, n; int b, loss;
-  uint64_t seed, problem, q0;
-  int64_t iters;
-  float alpha, c;
-  float *x;
-  unsigned *flag;
-};
-bool lowp_fits(int64_t n, int b);
-int launch_sgd_lowp(const LowpArgs &a, int dt, int acc_f16, cudaStream_t st);
-
 int launch_loss(Handle *h, const float *x, float lambda, cudaStream_t st);
 int launch_sample(uint64_t seed, uint64_t problem, int64_t first, int64_t count,
                   int64_t m, int32_t *out, cudaStream_t st);
