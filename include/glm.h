@@ -137,7 +137,10 @@ typedef struct {
                          0 (default) = automatic, else 1..16.                */
   int64_t chunk_outer;/* outer iterations staged per chunk; 0 = automatic.   */
   int gram_impl;      /* 0 (default) automatic, 1 SIMT FP32 kernel,
-                         2 tcgen05 tensor-core kernel.                        */
+                         2 tcgen05 tensor-core kernel, 3 SIMT kernel with
+                         FP16 accumulation (Recipe F's Gram slot: FP16
+                         input and accumulation; gram_dtype GLM_F16 only,
+                         else GLM_EINVAL; never chosen automatically).       */
   int timing;         /* 1: record CUDA events around every kernel of the run
                          (read back with glm_kernel_times).  Default 0.       */
 } glm_ca_opts;
@@ -150,7 +153,7 @@ typedef struct {
   int64_t chunks;       /* number of chunks                                   */
   int64_t launches;     /* kernels launched by the run                        */
   int cluster;          /* CTAs in the chain cluster                          */
-  int gram_impl;        /* 1 SIMT, 2 tcgen05                                  */
+  int gram_impl;        /* 1 SIMT, 2 tcgen05, 3 SIMT FP16 accumulation       */
   int gram_dtype, gemv_dtype, recurrence_f64;
 } glm_run_plan;
 
@@ -261,10 +264,14 @@ int glm_sample_indices_noalloc(uint64_t seed, uint32_t problem, int64_t first_dr
  * GLM_BF16, GLM_F16, GLM_E4M3 bytes); only the first n columns are read and
  * columns n..ld-1 must be zero.  row_scale: device FP32 per row (E4M3 only,
  * else NULL).  G: device FP32, for each group g the s(s-1)/2 blocks stored
- * row-block by row-block: row l of block row j (1 <= j < s) holds the j*b
- * values G[j b + l][0 .. j b) at offset g*b*b*s(s-1)/2 + b*b*j(j-1)/2 + l*j*b.
- * impl: 0 auto, 1 SIMT FP32, 2 tcgen05.  ld must be a multiple of 64 for
- * impl 2.  stream: cudaStream_t or NULL (legacy default stream).
+ * row-block by row-block with 16-byte aligned rows: with ld_t =
+ * 4 ceil(t b / 4), row l of block row j (1 <= j < s) holds the j*b values
+ * G[j b + l][0 .. j b) at float offset g Z + b (ld_1 + ... + ld_{j-1}) +
+ * l ld_j, where Z = b (ld_1 + ... + ld_{s-1}) floats per group; the padding
+ * floats of a row hold no result.  impl: 0 auto, 1 SIMT FP32, 2 tcgen05, 3
+ * SIMT with FP16 accumulation (GLM_F16 only, else GLM_EINVAL).  ld must be a
+ * multiple of 64 for impl 2.  stream: cudaStream_t or NULL (legacy default
+ * stream).
  */
 int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b,
                    int64_t n, int64_t ld, const float *row_scale, float *G,

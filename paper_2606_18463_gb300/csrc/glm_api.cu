@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "glm_internal.cuh"
-#include "glm_lowp.cuh"
+#include "glm_baselines.cuh"
 
 namespace glm {
 
@@ -163,8 +163,10 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   // Gram implementation
   if (o->gram_impl == 2 && !gram_tc_supported(gdt, p.ld_gram))
     return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram does not support this operand type");
+  if (o->gram_impl == 3 && gdt != GLM_F16)
+    return set_error(GLM_EINVAL, "gram_impl 3 (FP16 accumulation) needs gram_dtype GLM_F16");
   p.gram_impl = o->gram_impl == 0 ? (gram_tc_supported(gdt, p.ld_gram) ? 2 : 1) : o->gram_impl;
-  if (p.gram_impl != 1 && p.gram_impl != 2) return set_error(GLM_EINVAL, "gram_impl");
+  if (p.gram_impl < 1 || p.gram_impl > 3) return set_error(GLM_EINVAL, "gram_impl");
   // chunking
   p.H = (iters + s - 1) / s;
   const int64_t sb = (int64_t)s * b;
@@ -357,6 +359,7 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
       gr.flag = h->dflag;
       GLM_TRY(tmark(h, p, side, ci, 1, 0));
       if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, side));
+      else if (p.gram_impl == 3) GLM_TRY(launch_gram_simt_f16acc(gr, side));
       else GLM_TRY(launch_gram_simt(gr, side));
       GLM_TRY(tmark(h, p, side, ci, 1, 1));
     }
@@ -787,7 +790,11 @@ int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b, i
       return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram: unsupported type or ld % 64 != 0");
     return launch_gram_tc(a, st);
   }
-  if (impl != 1) return set_error(GLM_EINVAL, "impl must be 0, 1 or 2");
+  if (impl == 3) {
+    if (dtype != GLM_F16) return set_error(GLM_EINVAL, "impl 3 (FP16 accumulation) needs GLM_F16");
+    return launch_gram_simt_f16acc(a, st);
+  }
+  if (impl != 1) return set_error(GLM_EINVAL, "impl must be 0, 1, 2 or 3");
   return launch_gram_simt(a, st);
 }
 

@@ -1,6 +1,7 @@
-// glm_lowp.cuh -- host-side interface of the end-to-end low-precision
-// mini-batch SGD baseline (k_sgd_lowp.cu), kept apart from the shared header
-// of the CA-SGD path.
+// glm_baselines.cuh -- host-side interfaces of the numerical baselines of
+// the paper's recipe table, kept apart from the shared header of the CA-SGD
+// path: the end-to-end low-precision mini-batch SGD (k_sgd_lowp.cu) and the
+// FP16-accumulate Gram (k_gram_simt.cu).
 #pragma once
 
 #include "glm_internal.cuh"
@@ -21,5 +22,9 @@ struct LowpArgs {
 };
 bool lowp_fits(int64_t n, int b);
 int launch_sgd_lowp(const LowpArgs &a, int dt, int acc_f16, cudaStream_t st);
+
+// Strictly block-lower Gram of FP16 operands with FP16 accumulation (Recipe
+// F's Gram slot); GLM_EINVAL for other operand types or with row scales.
+int launch_gram_simt_f16acc(const GramArgs &a, cudaStream_t st);
 
 }  // namespace glm

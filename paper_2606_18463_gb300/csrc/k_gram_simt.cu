@@ -5,11 +5,17 @@
 // operand types: BF16 / F16 / TF32 / E4M3 products are exact in FP32, so only
 // the accumulation order differs from the tensor-core kernel.
 //
+// The same tiles with an FP16 accumulator (fused half multiply-adds, k in
+// ascending order for every output) give Recipe F's Gram slot: FP16 input
+// with FP16 accumulation (the h_a symbol of the paper's precision table).
+//
 // Tiles of 64 x 64 outputs over the lower triangle of each outer step's
 // (s b) x (s b) Gram; 256 threads, 4 x 4 outputs per thread, K staged 32 at a
 // time through shared memory (stored k-major so a thread reads 4 rows with
 // one 16-byte load).
-#include "glm_internal.cuh"
+#include <type_traits>
+
+#include "glm_baselines.cuh"
 
 namespace glm {
 namespace {
@@ -37,6 +43,7 @@ __device__ __forceinline__ void load8_any(const void *base, int dt, int64_t off,
   }
 }
 
+template <bool kAccF16>
 __global__ void __launch_bounds__(kThreads)
 k_gram_simt(GramArgs a) {
   const int64_t sb = (int64_t)a.s * a.b;
@@ -55,7 +62,12 @@ k_gram_simt(GramArgs a) {
   __shared__ __align__(16) float As[kK][kTile];
   __shared__ __align__(16) float Bs[kK][kTile];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][4] = {};
+  using Acc = typename std::conditional<kAccF16, __half, float>::type;
+  Acc acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0.f);
   const int eb = elem_bytes(a.dt);
   const char *Yg = static_cast<const char *>(a.Y) + g * sb * a.ld * eb;
   // loader mapping: 256 threads x 8 k-values = 64 rows x 32 k
@@ -89,7 +101,12 @@ k_gram_simt(GramArgs a) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) {
+          if constexpr (kAccF16)  // FP16 operands: the conversions are exact
+            acc[i][j] = __hfma(__float2half_rn(ar[i]), __float2half_rn(br[j]), acc[i][j]);
+          else
+            acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        }
     }
   }
   // epilogue: strictly block-lower entries into the row-block layout
@@ -105,7 +122,7 @@ k_gram_simt(GramArgs a) {
     for (int jj = 0; jj < 4; ++jj) {
       const int64_t col = c0 + tx * 4 + jj;
       if (col < j * a.b) {
-        float v = acc[i][jj];
+        float v = (float)acc[i][jj];
         if (a.rs) v = v * sr * a.rs[g * sb + col];
         grow[col] = v;
       }
@@ -113,9 +130,8 @@ k_gram_simt(GramArgs a) {
   }
 }
 
-}  // namespace
-
-int launch_gram_simt(const GramArgs &a, cudaStream_t st) {
+template <bool kAccF16>
+int launch_t(const GramArgs &a, cudaStream_t st) {
   if (a.s < 2 || a.nouter <= 0) return GLM_OK;
   const int64_t sb = (int64_t)a.s * a.b;
   const int64_t T = (sb + kTile - 1) / kTile;
@@ -123,9 +139,19 @@ int launch_gram_simt(const GramArgs &a, cudaStream_t st) {
   if (pairs > 0x7fffffff || a.nouter > 65535)
     return set_error(GLM_EINVAL, "gram: problem too large for one launch");
   dim3 grid((unsigned)pairs, (unsigned)a.nouter);
-  k_gram_simt<<<grid, kThreads, 0, st>>>(a);
+  k_gram_simt<kAccF16><<<grid, kThreads, 0, st>>>(a);
   GLM_CUDA_TRY(cudaGetLastError());
   return GLM_OK;
+}
+
+}  // namespace
+
+int launch_gram_simt(const GramArgs &a, cudaStream_t st) { return launch_t<false>(a, st); }
+
+int launch_gram_simt_f16acc(const GramArgs &a, cudaStream_t st) {
+  if (a.dt != GLM_F16 || a.rs)
+    return set_error(GLM_EINVAL, "FP16-accumulate Gram needs FP16 operands");
+  return launch_t<true>(a, st);
 }
 
 }  // namespace glm

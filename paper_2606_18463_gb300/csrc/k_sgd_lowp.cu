@@ -19,7 +19,7 @@
 // storage (each step's rows are read twice, the second time from L2).  This
 // path is a numerical baseline of the paper's, not a fast path: it keeps
 // nothing on the tensor cores and runs on one SM.
-#include "glm_lowp.cuh"
+#include "glm_baselines.cuh"
 
 namespace glm {
 namespace {

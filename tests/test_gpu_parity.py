@@ -271,6 +271,42 @@ def test_gram_lower_bound(G, dt, impl, nouter, s, b, n):
         assert np.all(err <= bound), (dt, impl, float(np.max(err - bound)))
 
 
+@pytest.mark.parametrize("nouter,s,b,n", [(3, 4, 16, 100), (2, 16, 64, 512), (1, 3, 130, 70)])
+def test_gram_lower_f16acc_bound(G, nouter, s, b, n):
+    # Recipe F's Gram slot: FP16 operands and FP16 accumulation by fused
+    # half multiply-adds, one rounding per step: |G^ - G| <= gamma_n(2^-11)
+    # |Y| |Y|^T entrywise (valid while n 2^-11 < 1)
+    rng = np.random.default_rng(s * 1000 + b + n + 7)
+    sb = s * b
+    ld = ((n + 63) // 64) * 64
+    vals = oracle.round_f16(rng.standard_normal((nouter * sb, n)).astype(np.float32))
+    dev = np.zeros((nouter * sb, ld), np.float32)
+    dev[:, :n] = vals
+    Yd = torch.from_numpy(dev).to(torch.float16).cuda()
+    Gd = torch.full((nouter * _gram_size(s, b),), float("nan"), dtype=torch.float32,
+                    device="cuda")
+    G.glm_gram_lower(Yd, G.GLM_F16, nouter, s, b, n, ld, None, Gd, 3)
+    torch.cuda.synchronize()
+    got = _unpack_gram(Gd.cpu().numpy().astype(np.float64), nouter, s, b)
+    u = 2.0 ** -11
+    gam = n * u / (1 - n * u)
+    vals = vals.astype(np.float64)
+    worst = 0.0
+    for g in range(nouter):
+        Yg = vals[g * sb:(g + 1) * sb]
+        ref = oracle.gram_lower(Yg, s, b)
+        bound = gam * oracle.gram_lower(np.abs(Yg), s, b) + 1e-30
+        err = np.abs(got[g] - ref)
+        assert np.all(err <= bound), float(np.max(err - bound))
+        worst = max(worst, float(np.max(err)))
+    assert worst > 0.0  # the accumulation is really FP16
+    # other operand types are rejected
+    Yb = torch.from_numpy(dev).to(torch.bfloat16).cuda()
+    with pytest.raises(G.GlmError) as e:
+        G.glm_gram_lower(Yb, G.GLM_BF16, nouter, s, b, n, ld, None, Gd, 3)
+    assert e.value.code == G.GLM_EINVAL
+
+
 # ----------------------------------------------------------------------------
 # Reduced precision: final risk within 1e-3 of the oracle's
 # ----------------------------------------------------------------------------
