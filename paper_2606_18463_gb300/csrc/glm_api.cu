@@ -487,7 +487,20 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
   h->dtype = dtype;
   h->lda = round_up(n, 8);
   int rc = GLM_OK;
+  // create-time temporaries: the input uploaded from the host, the column sums
+  void *tmpA = nullptr;
+  float *tmpy = nullptr;
+  double *acc = nullptr;
+  auto cleanup_tmp = [&]() {
+    if (tmpA) cudaFree(tmpA);
+    if (tmpy) cudaFree(tmpy);
+    if (acc) cudaFree(acc);
+    tmpA = nullptr;
+    tmpy = nullptr;
+    acc = nullptr;
+  };
   auto fail = [&](int code) {
+    cleanup_tmp();
     free_handle(h);
     return code;
   };
@@ -514,8 +527,6 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
   // input in device memory (temporary upload when it lives on the host)
   const void *src = A;
   const float *ysrc = y;
-  void *tmpA = nullptr;
-  float *tmpy = nullptr;
   const bool host_in = opts->input_on_host || !is_device_ptr(A);
   if (host_in) {
     CK(cudaMalloc(&tmpA, (size_t)m * n * ieb));
@@ -527,24 +538,18 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
     CK(cudaMemcpyAsync(tmpy, y, (size_t)m * 4, cudaMemcpyHostToDevice, st));
     ysrc = tmpy;
   }
-  auto cleanup_tmp = [&]() {
-    if (tmpA) cudaFree(tmpA);
-    if (tmpy) cudaFree(tmpy);
-    tmpA = nullptr;
-    tmpy = nullptr;
-  };
   CK(cudaMemcpyAsync(h->y, ysrc, (size_t)m * 4, cudaMemcpyDeviceToDevice, st));
   // per-column power-of-two scales (BF16 / F16 storage)
   if (dtype != GLM_F32 && opts->column_scales) {
-    double *acc = nullptr;
     CK(cudaMalloc(&acc, (size_t)n * 8));
     CK(cudaMemsetAsync(acc, 0, (size_t)n * 8, st));
     rc = launch_colsumsq(src, opts->input_dtype, m, n, acc, st);
-    if (rc != GLM_OK) { cudaFree(acc); cleanup_tmp(); return fail(rc); }
+    if (rc != GLM_OK) return fail(rc);
     std::vector<double> hs(n);
     CK(cudaMemcpyAsync(hs.data(), acc, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     cudaFree(acc);
+    acc = nullptr;
     std::vector<float> kappa(h->lda, 1.0f);
     for (int64_t k = 0; k < n; ++k) {
       const double rms = sqrt(hs[k] / (double)m);
@@ -556,16 +561,16 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
     CK(cudaStreamSynchronize(st));
   }
   rc = launch_create_convert(h, src, opts->input_dtype, 0, m, st);
-  if (rc != GLM_OK) { cleanup_tmp(); return fail(rc); }
+  if (rc != GLM_OK) return fail(rc);
   if (opts->fp8_copy) {
     h->lda8 = round_up(n, 16);
     CK(cudaMalloc(&h->A8, (size_t)m * h->lda8));
     CK(cudaMalloc(&h->rowscale8, (size_t)m * 4));
     rc = launch_fp8_copy(h, src, opts->input_dtype, 0, m, st);
-    if (rc != GLM_OK) { cleanup_tmp(); return fail(rc); }
+    if (rc != GLM_OK) return fail(rc);
   }
   rc = launch_check_labels(h->y, m, loss, h->dflag, st);
-  if (rc != GLM_OK) { cleanup_tmp(); return fail(rc); }
+  if (rc != GLM_OK) return fail(rc);
   unsigned flag = 0;
   CK(cudaMemcpyAsync(&flag, h->dflag, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
