@@ -52,6 +52,31 @@ def test_sgd_lsq_exact_rational():
     assert np.max(np.abs(got - exact)) <= 1e-14 * max(1.0, np.max(np.abs(exact)))
 
 
+def test_sgd_first_iter_exact_rational_and_resume():
+    # iteration t of a run started at first_iter draws rows (first_iter + t) b ..
+    # + b - 1 (Algorithm 1, sampling step on a counter-based stream), from any x0
+    A, y = _tiny(8, 3, seed=2, loss=LSQ)
+    b, eta, lam, T, seed, k0 = 2, 0.25, 0.5, 6, 7, 5
+    x0 = np.array([0.5, -0.25, 0.125])
+    Af = [[Fraction(float(v)) for v in row] for row in A]
+    yf = [Fraction(float(v)) for v in y]
+    x = [Fraction(float(v)) for v in x0]
+    alpha, c = Fraction(eta) / b, 1 - Fraction(eta) * Fraction(lam)
+    for t in range(T):
+        idx = oracle.sample_indices(seed, 0, (k0 + t) * b, b, 8)
+        u = [sum(Af[i][k] * x[k] for k in range(3)) - yf[i] for i in idx]
+        g = [sum(Af[i][k] * u[l] for l, i in enumerate(idx)) for k in range(3)]
+        x = [c * x[k] - alpha * g[k] for k in range(3)]
+    exact = np.array([float(v) for v in x])
+    got = oracle.sgd(A, y, LSQ, b, eta, lam, T, seed, x0=x0, first_iter=k0)
+    assert np.max(np.abs(got - exact)) <= 1e-14 * max(1.0, np.max(np.abs(exact)))
+    # a run of k + l iterations is a run of k followed by one of l from k
+    xa = oracle.sgd(A, y, LSQ, b, eta, lam, k0, seed)
+    xb = oracle.sgd(A, y, LSQ, b, eta, lam, T, seed, x0=xa, first_iter=k0)
+    xc = oracle.sgd(A, y, LSQ, b, eta, lam, k0 + T, seed)
+    assert np.array_equal(xb, xc)
+
+
 def test_sgd_logistic_mpmath():
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 60
