@@ -21,6 +21,8 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   ridge_closed_form pinned (stationarity of the independently coded gradient).
   gram_lower ...... pinned (element-wise brute force).
   round_* ......... pinned (numpy float16 cast, exhaustive bit-pattern checks).
+  column_scales ... pinned (closed forms: RMS against mean |a|, rounding of the
+                    log2 against flooring, the all-zero column).
 
 ``oracle.local_error`` (numpy) evaluates the first-order local error budget of
 one outer step (Theorem 1, Sec. 5.2) and simulates that step with each

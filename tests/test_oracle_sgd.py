@@ -378,6 +378,19 @@ def test_round_e4m3_table():
             assert g in best
 
 
+def test_column_scales_closed_forms():
+    # kappa_j = 2^round(log2 RMS_j) (per-column power-of-two scale, storage of
+    # Table 1 with scales); 1 for an all-zero column
+    A = np.array([[3.0, 0.0, 2.0 ** -5, 0.0, 0.7],
+                  [3.0, 0.0, -2.0 ** -5, 0.0, -0.7],
+                  [3.0, 0.0, 2.0 ** -5, 0.0, 0.7],
+                  [3.0, 0.0, -2.0 ** -5, 8.0, -0.7]])
+    # RMS 3 -> log2 1.58 -> 4 (a floor would give 2); zero column -> 1;
+    # RMS 2^-5 exactly; RMS of (0, 0, 0, 8) is 4 (its mean |a| is 2);
+    # RMS 0.7 -> log2 -0.51 -> 1/2
+    assert np.array_equal(oracle.column_scales(A), [4.0, 1.0, 2.0 ** -5, 4.0, 0.5])
+
+
 def test_fp8_row_scales_exact():
     A = np.array([[448.0, 1.0], [449.0, 0.0], [0.0, 0.0], [-0.001, 0.0005], [896.0, 1.0]])
     rho = oracle.fp8_row_scales(A)
