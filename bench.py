@@ -266,8 +266,7 @@ def main():
     ds = glm.Dataset(A, y, pr.loss, "f32", stream=stream)
     del A, y
     x = torch.zeros(pr.n, dtype=torch.float32, device="cuda")
-    opts = dict(gram_dtype=args.gram, cluster=args.cluster, timing=1, seed_rank=rank)
-    opts.pop("seed_rank")
+    opts = dict(gram_dtype=args.gram, cluster=args.cluster, timing=1)
     seed = replica_seed(w["seed"], rank)
     plan = glm.glm_ca_plan(ds.h, s, b, w["eta"], w["lam"], T, glm.default_ca_opts(**opts))
 
