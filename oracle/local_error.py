@@ -19,20 +19,23 @@ Slots (Sec. 3, the nine operations of an outer step): u_A storage of Y, the
 margin GEMV (factor gamma_r), the Gram (gamma_G), the correction recurrence
 u_c, the residual u_sigma, the gradient GEMV (gamma_g), the master weights
 u_x, and the two all-reduces (C(P) u_AR,r and C(P) u_AR,G; zero on one GPU).
+The simulator can split the columns over P ranks to exercise the last two.
 
 Parity status (pins in ``tests/test_oracle_local_error.py``):
   fl .............. pinned (numpy's float32 and float16 casts, the BF16 rounding).
   exact_step ...... pinned (the C oracle's SGD on the same index stream; the
                     residual against the C oracle's loss derivative).
   simulate_step ... pinned (without rounding it equals exact_step: CA-SGD and
-                    SGD agree in exact arithmetic).
+                    SGD agree in exact arithmetic; one rank needs no reduction).
   local_error ..... pinned (K_s by the terminating Neumann series and a 2 x 2
                     closed form; H_L, T_g, T_r, T_G, T_c by element loops;
                     each term bounds the deviation the simulator shows with
                     its slot alone rounded, sits within a fixed factor of it
                     under directed rounding, and equals it to first order in
                     cases where every inequality behind the term is tight;
-                    all slots together stay within the first-order sum).
+                    all slots together stay within the first-order sum; the
+                    two all-reduce terms likewise, against a simulation over
+                    P ranks).
                     Not pinned: the factor K_s in E_sigma, which no case makes
                     tight (the residual's slope reaches L_sigma only near zero
                     margin, its size reaches D_delta only far from it).
@@ -48,7 +51,7 @@ LOGISTIC, LSQ = 0, 1
 # L_sigma, the Lipschitz constant of the residual in the margin (Assumption 2)
 LIPSCHITZ = {LOGISTIC: 0.25, LSQ: 1.0}
 
-SLOTS = ("A", "r", "G", "c", "sigma", "g", "x")
+SLOTS = ("A", "r", "G", "c", "sigma", "g", "x", "AR_r", "AR_G")
 
 
 # --------------------------------------------------------------------------
@@ -153,28 +156,45 @@ def _gram(Y, p, mode):
     return acc
 
 
+def _allreduce(parts, p, mode):
+    """Sum of the ranks' partial arrays, rank by rank, each addition rounded
+    to p bits: |error| <= gamma_{P-1} sum_p |part_p| (one rank: no rounding)."""
+    acc = parts[0]
+    for v in parts[1:]:
+        acc = fl(acc + v, p, mode)
+    return acc
+
+
 def simulate_step(Y, yI, x, loss: int, eta: float, s: int, b: int, prec=None,
-                  mode: str = "nearest"):
+                  mode: str = "nearest", P: int = 1):
     """One CA-SGD outer step from x in the order of the outer iteration of
     Sec. 4 (Algorithm 1): rows stored (slot A), base margins r = Y x (r),
     Gram G = Y Y^T (G), then for each inner step j the correction
     z_j = r_j + alpha sum_{i<j} G_{j,i} d_i (c) and the residual
     d_j = delta(z_j) (sigma), the gradient Y^T d (g) and the update
     x + alpha Y^T d (x).  ``prec`` maps a slot name to the bits its
-    operations keep; a missing slot is exact.  lambda = 0."""
+    operations keep; a missing slot is exact.  lambda = 0.
+
+    With P > 1 the columns are split into P contiguous slabs, one per rank
+    (the paper's 1D block-column partition): each rank forms its partial
+    margins and Gram over its slab, and the all-reduces sum them rank by rank
+    (slots AR_r and AR_G).  The gradient and the update of each slab stay on
+    its rank and need no reduction."""
     prec = dict(prec or {})
     bad = set(prec) - set(SLOTS)
     if bad:
         raise ValueError(f"unknown slots {sorted(bad)}")
-    P = lambda k: prec.get(k)  # noqa: E731
+    bits = lambda k: prec.get(k)  # noqa: E731
     alpha = eta / b
-    Y = fl(np.asarray(Y, dtype=np.float64), P("A"), mode)
+    Y = fl(np.asarray(Y, dtype=np.float64), bits("A"), mode)
     yI = np.asarray(yI, dtype=np.float64)
     x = np.asarray(x, dtype=np.float64)
-    r = _dot_rows(Y, x, P("r"), mode)
-    G = _gram(Y, P("G"), mode)
+    slabs = np.array_split(np.arange(Y.shape[1]), P)
+    r = _allreduce([_dot_rows(Y[:, c], x[c], bits("r"), mode) for c in slabs],
+                   bits("AR_r"), mode)
+    G = _allreduce([_gram(Y[:, c], bits("G"), mode) for c in slabs], bits("AR_G"), mode)
     d = np.zeros(s * b)
-    pc = P("c")
+    pc = bits("c")
     for j in range(s):
         rows = slice(j * b, (j + 1) * b)
         if j == 0:
@@ -182,9 +202,9 @@ def simulate_step(Y, yI, x, loss: int, eta: float, s: int, b: int, prec=None,
         else:
             t = _dot_rows(G[rows, :j * b], d[:j * b], pc, mode)
             z = fl(r[rows] + fl(alpha * t, pc, mode), pc, mode)
-        d[rows] = fl(residual(loss, z, yI[rows]), P("sigma"), mode)
-    g = _dot_rows(Y.T, d, P("g"), mode)
-    px = P("x")
+        d[rows] = fl(residual(loss, z, yI[rows]), bits("sigma"), mode)
+    g = _dot_rows(Y.T, d, bits("g"), mode)
+    px = bits("x")
     return fl(x + fl(alpha * g, px, mode), px, mode)
 
 

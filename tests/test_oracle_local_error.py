@@ -18,6 +18,9 @@ Sec. 5.2) and for its rounding simulator (``oracle.local_error``).
     two inner steps, least squares, the rounding model's extreme v (1 + u)
     for every operation): the deviation equals the term to first order, so
     a wrong factor or source quantity in any term fails;
+  * the two all-reduce terms against a simulation that splits the columns
+    over P ranks and rounds only the reduction (bounds, floors, tight
+    two-rank cases);
   * all slots rounded together within twice the sum;
   * the Recipe C hypothesis figure printed in Sec. 5.3.
 """
@@ -186,17 +189,22 @@ def test_single_inner_step_degenerates():
 # ----------------------------------------------------------------------------
 # Each term against the simulator
 # ----------------------------------------------------------------------------
-KEY = dict(A="E_A", r="E_r", G="E_G", c="E_c", sigma="E_sigma", g="E_g", x="E_x")
+KEY = dict(A="E_A", r="E_r", G="E_G", c="E_c", sigma="E_sigma", g="E_g", x="E_x",
+           AR_r="E_AR_r", AR_G="E_AR_G")
+ONE_RANK = [sl for sl in le.SLOTS if not sl.startswith("AR")]
 # smallest deviation / term under directed rounding seen over seeds 0..19 of
 # _problem is 3.2 times or more above these floors (both losses, p = 8 and 11)
-FLOOR = dict(A=1e-2, r=5e-3, G=1e-3, c=5e-3, sigma=2e-3, g=1e-2, x=5e-2)
+FLOOR = dict(A=1e-2, r=5e-3, G=1e-3, c=5e-3, sigma=2e-3, g=1e-2, x=5e-2,
+             AR_r=5e-3, AR_G=1e-3)  # the last two: 3.7 times or more, P in {2, 3, 6}
 
 
-def _slot_args(slot, u, n, sb):
+def _slot_args(slot, u, n, sb, P=1):
+    # the all-reduce sums its P partials rank by rank: C(P) u = gamma_{P-1}(u)
     return {"A": dict(u_A=u), "r": dict(gamma_r=le.gamma(n, u)),
             "G": dict(gamma_G=le.gamma(n, u)), "c": dict(u_c=u),
             "sigma": dict(u_sigma=u), "g": dict(gamma_g=le.gamma(sb, u)),
-            "x": dict(u_x=u)}[slot]
+            "x": dict(u_x=u), "AR_r": dict(cP_u_AR_r=le.gamma(P - 1, u)),
+            "AR_G": dict(cP_u_AR_G=le.gamma(P - 1, u))}[slot]
 
 
 @pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
@@ -207,7 +215,7 @@ def test_each_term_bounds_its_slot(loss, mode, p):
     u = le.unit_roundoff(p, mode)
     for seed in range(8):
         Y, y, x = _problem(seed, loss, n, s, b)
-        for slot in le.SLOTS:
+        for slot in ONE_RANK:
             ev = le.local_error(Y, y, x, loss, eta, s, b, **_slot_args(slot, u, n, s * b))
             assert ev["omega"] <= 0.5 and ev["tau_G"] <= 0.5
             dev = np.linalg.norm(le.simulate_step(Y, y, x, loss, eta, s, b, {slot: p}, mode)
@@ -284,11 +292,63 @@ def test_first_order_terms_bound_the_rounding_model_extreme(loss):
     for seed in range(10):
         for n, s, b in ((24, 4, 4), (8, 6, 2), (40, 3, 8)):
             Y, y, x = _problem(200 + seed, loss, n, s, b)
-            for slot in le.SLOTS:
+            for slot in ONE_RANK:
                 ev = le.local_error(Y, y, x, loss, 0.5, s, b, **_slot_args(slot, u, n, s * b))
                 dev = np.linalg.norm(le.simulate_step(Y, y, x, loss, 0.5, s, b,
                                                       {slot: TIGHT_P}, "model") - ev["x_s"])
                 assert dev <= (1 + 1e-3) * ev[KEY[slot]], (slot, seed, n, s, b)
+
+
+@pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
+@pytest.mark.parametrize("mode,p", [("nearest", 8), ("nearest", 11), ("up", 8), ("up", 11),
+                                    ("model", TIGHT_P)])
+def test_allreduce_terms_bound_their_slots(loss, mode, p):
+    # the columns split over P ranks; only the all-reduce of the partial
+    # margins (AR_r) or Gram blocks (AR_G) rounds
+    n, s, b, eta = 24, 4, 4, 0.5
+    u = le.unit_roundoff(p, mode)
+    for P in (2, 3, 6):
+        for seed in range(8):
+            Y, y, x = _problem(seed, loss, n, s, b)
+            for slot in ("AR_r", "AR_G"):
+                ev = le.local_error(Y, y, x, loss, eta, s, b, **_slot_args(slot, u, n, s * b, P))
+                dev = np.linalg.norm(le.simulate_step(Y, y, x, loss, eta, s, b, {slot: p}, mode,
+                                                      P=P) - ev["x_s"])
+                E = ev[KEY[slot]]
+                bound = (1 + 1e-3) * E if mode == "model" else 2 * E
+                assert 0 < dev <= bound, (slot, P, seed, dev, E)
+                if mode == "up":
+                    assert dev >= FLOOR[slot] * E, (slot, P, seed, dev / E)
+    # one rank: no reduction, nothing rounds
+    Y, y, x = _problem(0, loss, n, s, b)
+    _, _, xs = le.exact_step(Y, y, x, loss, eta, s, b)
+    xh = le.simulate_step(Y, y, x, loss, eta, s, b, {"AR_r": 8, "AR_G": 8}, mode, P=1)
+    assert np.allclose(xh, xs[-1], rtol=0, atol=1e-13)
+
+
+def test_allreduce_terms_are_attained_in_tight_cases():
+    # two ranks of one column each; the partial sums share their sign, so the
+    # reduction's rounding meets C(P) u sum_p |v_p| with C(2) u = gamma_1(u)
+    u = le.unit_roundoff(TIGHT_P, "model")
+    g1 = le.gamma(1, u)
+
+    def ratio(slot, Y, y, x, eta, s, b, loss=le.LSQ, **f):
+        Y, y, x = (np.array(v, dtype=float) for v in (Y, y, x))
+        ev = le.local_error(Y, y, x, loss, eta, s, b, **f)
+        xh = le.simulate_step(Y, y, x, loss, eta, s, b, {slot: TIGHT_P}, "model", P=2)
+        return np.linalg.norm(xh - ev["x_s"]) / ev[KEY[slot]]
+
+    # one step, one row: r = a_0 x_0 + a_1 x_1 with both products positive
+    assert ratio("AR_r", [[0.6, 0.8]], [2.0], [0.5, 0.25], 0.5, 1, 1,
+                 cP_u_AR_r=g1) == pytest.approx(1, abs=1e-4)
+    # logistic near zero margin: the residual's slope reaches L_sigma = 1/4
+    assert ratio("AR_r", [[0.6, 0.8]], [1.0], [1e-3, 1e-3], 0.5, 1, 1, loss=le.LOGISTIC,
+                 cP_u_AR_r=g1) == pytest.approx(1, abs=1e-4)
+    # two steps from x = 0 with a tiny first row: G_10 = a_10 a_00 + a_11 a_01
+    # with both products positive, and ||Y||_2 K_s -> ||a_1|| = 1
+    h = 1 / math.sqrt(2)
+    assert ratio("AR_G", [[1e-3, 1e-3], [h, h]], [1.0, 0.3], [0.0, 0.0], 0.125, 2, 1,
+                 cP_u_AR_G=g1) == pytest.approx(1, abs=1e-4)
 
 
 @pytest.mark.parametrize("loss", [le.LOGISTIC, le.LSQ])
