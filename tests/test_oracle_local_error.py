@@ -170,9 +170,19 @@ def test_K_s_two_by_two_closed_form(loss, L):
     Y = np.array([[0.6, 0.8], [0.6, 0.8]])
     ev = le.local_error(Y, np.array([1.0, -1.0]), np.array([0.3, -0.2]), loss, eta, 2, 1)
     a = L * eta
-    assert ev["K_s"] == pytest.approx((a + math.sqrt(a * a + 4)) / 2, rel=1e-14)
+    K = (a + math.sqrt(a * a + 4)) / 2
+    assert ev["K_s"] == pytest.approx(K, rel=1e-14)
     assert ev["norm_H_L"] == pytest.approx(1.0, rel=1e-14)
     assert ev["norm_Y"] == pytest.approx(math.sqrt(2), rel=1e-14)
+    # the hypothesis figures with these K_s and ||H_L||_2 = 1 (alpha = eta, b = 1):
+    # tau_G = K_s L_sigma alpha (2 u_A + gamma_G + C(P) u_AR,G) ||H_L||_2, omega the
+    # largest slot factor (gamma_{(s-1)b}(u_c) for the recurrence)
+    f = dict(u_A=1e-3, gamma_r=4e-3, gamma_G=2e-3, u_c=1e-2, u_sigma=5e-4, gamma_g=3e-3,
+             u_x=1e-4, cP_u_AR_r=6e-3, cP_u_AR_G=3e-3)
+    ev = le.local_error(Y, np.array([1.0, -1.0]), np.array([0.3, -0.2]), loss, eta, 2, 1, **f)
+    assert ev["tau_G"] == pytest.approx(K * L * eta * (2e-3 + 2e-3 + 3e-3), rel=1e-14)
+    assert ev["omega"] == pytest.approx(1e-2 / (1 - 1e-2), rel=1e-14)
+    assert ev["Omega"] == max(ev["omega"], ev["tau_G"])
 
 
 def test_single_inner_step_degenerates():
