@@ -35,10 +35,11 @@ Parity status (pins in ``tests/test_oracle_local_error.py``):
                     cases where every inequality behind the term is tight;
                     all slots together stay within the first-order sum; the
                     two all-reduce terms likewise, against a simulation over
-                    P ranks).
-                    Not pinned: the factor K_s in E_sigma, which no case makes
+                    P ranks).  The factor K_s in E_sigma, which no case makes
                     tight (the residual's slope reaches L_sigma only near zero
-                    margin, its size reaches D_delta only far from it).
+                    margin, its size reaches D_delta only far from it), is
+                    pinned by a case with amplifying inner steps (alpha a^2 =
+                    3) whose deviation exceeds the term without K_s.
 """
 from __future__ import annotations
 

@@ -18,6 +18,8 @@ Sec. 5.2) and for its rounding simulator (``oracle.local_error``).
     two inner steps, least squares, the rounding model's extreme v (1 + u)
     for every operation): the deviation equals the term to first order, so
     a wrong factor or source quantity in any term fails;
+  * E_sigma's factor K_s, with inner steps that amplify errors: the
+    deviation exceeds the term without K_s;
   * the two all-reduce terms against a simulation that splits the columns
     over P ranks and rounds only the reduction (bounds, floors, tight
     two-rank cases);
@@ -280,6 +282,40 @@ def test_terms_are_attained_in_tight_cases():
     # the looseness of ||Y||_2 K_s (0.93 of the term here)
     r = _tight("A", [[1e-3], [1.0]], [1.0, 16.0 * 1e-3], [0.0], 16.0, 2, 1, u_A=u)
     assert 0.9 <= r <= 1.0, r
+
+
+def test_K_s_in_E_sigma_is_needed_when_steps_amplify():
+    # E_sigma's factor K_s carries each residual's rounding error through the
+    # later inner steps of the recurrence.  With stable steps those steps
+    # contract (|1 - alpha a^2| <= 1) and the term holds without K_s; here
+    # alpha a^2 = 3, so each later step multiplies an error by -2.  One column
+    # of ones, b = 1, x_0 = 1 and labels +-1/3 give iterates +-1 and residuals
+    # -+2/3 whose errors all add up: the first-order deviation is
+    # 2 u (2^s - 1), against alpha ||Y||_2 u D_delta sqrt(sb) = 4 s u without
+    # K_s.  The term with K_s (the series 1, 3, 12, 48, ... of
+    # (I - alpha |G_L|)^-1) bounds it; without K_s it does not.
+    u = le.unit_roundoff(TIGHT_P, "model")
+    for s in (4, 6, 8):
+        Y = np.ones((s, 1))
+        y = np.array([(-1.0) ** j / 3.0 for j in range(s)])
+        x = np.array([1.0])
+        ev = le.local_error(Y, y, x, le.LSQ, 3.0, s, 1, u_sigma=u)
+        assert ev["omega"] <= 0.5 and ev["tau_G"] <= 0.5
+        assert ev["D_delta"] == pytest.approx(4.0 / 3.0) and ev["R"] == pytest.approx(1.0)
+        dev = np.linalg.norm(le.simulate_step(Y, y, x, le.LSQ, 3.0, s, 1, {"sigma": TIGHT_P},
+                                              "model") - ev["x_s"])
+        assert dev / u == pytest.approx(2 * (2 ** s - 1), rel=1e-4)
+        without_K = ev["E_sigma"] / ev["K_s"]
+        assert without_K / u == pytest.approx(4 * s, rel=1e-12)
+        assert dev > 1.8 * without_K, (s, dev / without_K)
+        assert dev <= ev["E_sigma"], (s, dev / ev["E_sigma"])
+        # K_s is the norm of the unit lower triangular Toeplitz inverse whose
+        # first column is 1, 3, 12, 48, ... (c_k = 3 sum_{i<k} c_i)
+        c = [1.0]
+        for _ in range(1, s):
+            c.append(3.0 * sum(c))
+        T = np.array([[c[i - j] if i >= j else 0.0 for j in range(s)] for i in range(s)])
+        assert ev["K_s"] == pytest.approx(np.linalg.norm(T, 2), rel=1e-10)
 
 
 def test_logistic_slope_is_attained_near_zero_margin():
