@@ -91,8 +91,9 @@ void glm_create_opts_default(glm_create_opts *o);
  * device storage of element type `dtype` (GLM_F32, GLM_BF16 or GLM_F16),
  * paper Table 1 slot u_A; labels stay FP32.  The caller keeps ownership of
  * A and y.  Requires 1 <= m < 2^31, 1 <= n <= 65536, loss GLM_LOGISTIC
- * (labels exactly +-1, else GLM_EINVAL) or GLM_LSQ.  Blocks until the copy
- * and conversion are done.  glm_create takes device FP32 pointers.
+ * (labels exactly +-1), GLM_LSQ (finite labels) or GLM_POISSON (finite
+ * labels >= 0); other labels give GLM_EINVAL.  Blocks until the copy and
+ * conversion are done.  glm_create takes device FP32 pointers.
  */
 int glm_create(const float *A, const float *y, int64_t m, int64_t n, int loss,
                int dtype, glm_handle *out);
@@ -215,7 +216,10 @@ int glm_sgd_lowp_run(glm_handle h, int64_t b, float eta, float lambda,
  * and applies x <- c^s x - alpha sum_j c^{s-1-j} Y_j^T u_j.  In exact
  * arithmetic this equals s SGD iterations on the same draws (paper
  * Assumption 6).  If iters % s != 0 the last outer iteration has
- * iters % s inner steps.  x: device FP32[n], in/out.
+ * iters % s inner steps.  x: device FP32[n], in/out.  0 <= eta*lambda < 1;
+ * the recurrence carries the residual history scaled by c^-j, so a request
+ * with c^-(s-1) > 2^60 (eta*lambda near 1 with a long s, e.g. eta*lambda
+ * above about 0.48 at s = 64) returns GLM_EUNSUPPORTED before any work.
  */
 int glm_ca_sgd_run(glm_handle h, int s, int64_t b, float eta, float lambda,
                    int64_t iters, uint64_t seed, float *x);
@@ -249,13 +253,42 @@ int glm_sample_indices(uint64_t seed, uint32_t problem, int64_t first_draw,
  * before any device work.  Calls whose work overlaps on the same GPU race on
  * the shared staging array: serialise them.  The first call on a device
  * resolves the array's address (cudaGetSymbolAddress, with that device
- * current): make it before any stream capture.  Blocks.
+ * current): make it before any stream capture.  The address is kept for the
+ * life of the process, so do not call this on a device after a
+ * cudaDeviceReset of it.  A device (or managed) out pointer returns
+ * GLM_EINVAL.  Blocks.
  */
 #define GLM_SAMPLE_NOALLOC_MAX 1048576
 int glm_sample_indices_noalloc(uint64_t seed, uint32_t problem, int64_t first_draw,
                                int64_t count, int64_t m, int32_t *out);
 
 /* ---- kernel-level entry points (tests, micro-benchmarks) ----------------- */
+
+/*
+ * Layout of the dataset a handle stores (Table 1 slot u_A, created by
+ * glm_create_ex): *dtype = GLM_F32, GLM_BF16 or GLM_F16; *lda = row stride in
+ * elements (n rounded up to a multiple of 8; columns n..lda-1 hold zeros);
+ * *lda8 = row stride in bytes of the optional FP8-E4M3 copy (n rounded up to
+ * a multiple of 16; 0 when there is none).  Any output may be NULL.
+ */
+int glm_storage_layout(glm_handle h, int *dtype, int64_t *lda, int64_t *lda8);
+
+/*
+ * Copy rows [row0, row0 + rows) of what glm_create_ex stored to HOST memory,
+ * so that the create-time quantisation can be checked value by value.  Each
+ * output may be NULL (skipped):
+ *   A_out         rows x lda elements of the storage type, as stored (A / kappa
+ *                 rounded to nearest even, kappa the column scale);
+ *   colscale_out  n floats: the power-of-two column scales kappa_j (all 1
+ *                 when the handle keeps none, e.g. FP32 storage);
+ *   fp8_out       rows x lda8 E4M3 bytes (E4M3(a / rho_i), nearest even,
+ *                 saturating); GLM_EINVAL if the handle has no FP8 copy;
+ *   rowscale_out  rows floats: the FP8 copy's power-of-two row scales rho_i;
+ *                 GLM_EINVAL if the handle has no FP8 copy.
+ * Requires 0 <= row0, rows >= 0, row0 + rows <= m.  Blocks.
+ */
+int glm_storage_read(glm_handle h, int64_t row0, int64_t rows, void *A_out,
+                     float *colscale_out, uint8_t *fp8_out, float *rowscale_out);
 
 /*
  * Strictly block-lower Gram (paper Algorithm 1, Gram step; Sec. 5.2 G_L) of
@@ -289,7 +322,7 @@ typedef struct {
   const void *A;     /* m x n, element type input_dtype, host or device    */
   const float *y;    /* m labels                                           */
   int64_t m, n;      /* 1 <= m < 2^31, 1 <= n <= 16384                     */
-  int loss;          /* GLM_LOGISTIC or GLM_LSQ                            */
+  int loss;          /* GLM_LOGISTIC, GLM_LSQ or GLM_POISSON              */
   float lambda, eta;
   int64_t iters;     /* SGD-equivalent iterations (0: the problem is idle) */
   uint64_t seed;

@@ -765,6 +765,50 @@ int glm_sample_indices(uint64_t seed, uint32_t problem, int64_t first_draw, int6
   return rc;
 }
 
+int glm_storage_layout(glm_handle hh, int *dtype, int64_t *lda, int64_t *lda8) {
+  g_last_error.clear();
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h) return set_error(GLM_EINVAL, "null handle");
+  if (dtype) *dtype = h->dtype;
+  if (lda) *lda = h->lda;
+  if (lda8) *lda8 = h->A8 ? h->lda8 : 0;
+  return GLM_OK;
+}
+
+int glm_storage_read(glm_handle hh, int64_t row0, int64_t rows, void *A_out,
+                     float *colscale_out, uint8_t *fp8_out, float *rowscale_out) {
+  g_last_error.clear();
+  Handle *h = reinterpret_cast<Handle *>(hh);
+  if (!h) return set_error(GLM_EINVAL, "null handle");
+  if (row0 < 0 || rows < 0 || row0 + rows > h->m)
+    return set_error(GLM_EINVAL, "rows [row0, row0 + rows) must lie in [0, m)");
+  if ((fp8_out || rowscale_out) && !h->A8)
+    return set_error(GLM_EINVAL, "the handle keeps no FP8 copy (create it with fp8_copy = 1)");
+  for (const void *p : {(const void *)A_out, (const void *)colscale_out, (const void *)fp8_out,
+                        (const void *)rowscale_out})
+    if (p && is_device_ptr(p)) return set_error(GLM_EINVAL, "outputs must be host memory");
+  cudaStream_t st = h->stream;
+  const int eb = elem_bytes(h->dtype);
+  if (A_out && rows > 0)
+    GLM_CUDA_TRY(cudaMemcpyAsync(A_out, static_cast<const char *>(h->A) + row0 * h->lda * eb,
+                                 (size_t)rows * h->lda * eb, cudaMemcpyDeviceToHost, st));
+  if (colscale_out) {
+    if (h->colscale)
+      GLM_CUDA_TRY(cudaMemcpyAsync(colscale_out, h->colscale, (size_t)h->n * 4,
+                                   cudaMemcpyDeviceToHost, st));
+    else
+      for (int64_t k = 0; k < h->n; ++k) colscale_out[k] = 1.0f;
+  }
+  if (fp8_out && rows > 0)
+    GLM_CUDA_TRY(cudaMemcpyAsync(fp8_out, h->A8 + row0 * h->lda8, (size_t)rows * h->lda8,
+                                 cudaMemcpyDeviceToHost, st));
+  if (rowscale_out && rows > 0)
+    GLM_CUDA_TRY(cudaMemcpyAsync(rowscale_out, h->rowscale8 + row0, (size_t)rows * 4,
+                                 cudaMemcpyDeviceToHost, st));
+  GLM_CUDA_TRY(cudaStreamSynchronize(st));
+  return GLM_OK;
+}
+
 int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b, int64_t n,
                    int64_t ld, const float *row_scale, float *G, int impl, void *stream) {
   g_last_error.clear();

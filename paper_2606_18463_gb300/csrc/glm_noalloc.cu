@@ -1,5 +1,5 @@
 // glm_noalloc.cu -- glm_sample_indices_noalloc: the host-output form of the
-// index-stream draw (Sec. 5.1's sampler, Philox4x64-10 mapped to
+// index-stream draw (Algorithm 1's sampling step: Philox4x64-10 mapped to
 // floor(U m / 2^64)) with its device staging buffer held in a fixed
 // file-scope __device__ array instead of a per-call cudaMalloc/cudaFree.
 //
@@ -7,7 +7,9 @@
 // calls whose work overlaps on the same GPU race on it; callers serialise
 // them.  The first call on a device resolves the array's address with
 // cudaGetSymbolAddress (which may load this module), so make that first call
-// before any stream capture begins.
+// before any stream capture begins.  The resolved address is kept for the
+// life of the process: cudaDeviceReset ends the context it belongs to, so the
+// entry point must not be called on a device after that device was reset.
 #include <mutex>
 
 #include "glm_internal.cuh"
@@ -57,6 +59,15 @@ extern "C" int glm_sample_indices_noalloc(uint64_t seed, uint32_t problem, int64
                           "GLM_SAMPLE_NOALLOC_MAX (1048576) indices");
   if (count == 0) return GLM_OK;
   if (!out) return glm::set_error(GLM_EINVAL, "out is NULL");
+  {  // the output must be host memory (a device pointer would make the copy
+     // below a device-to-device copy described as device-to-host)
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, out) != cudaSuccess) {
+      cudaGetLastError();
+    } else if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+      return glm::set_error(GLM_EINVAL, "glm_sample_indices_noalloc: out must be host memory");
+    }
+  }
   int32_t *d = nullptr;
   GLM_TRY(scratch_for_current_device(&d));
   GLM_TRY(glm::launch_sample(seed, problem, first_draw, count, m, d, 0));

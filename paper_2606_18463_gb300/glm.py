@@ -37,6 +37,7 @@ EXPORTED = [
     "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_sgd_lowp_run", "glm_ca_sgd_run",
     "glm_ca_sgd_run_ex", "glm_ca_plan", "glm_kernel_times", "glm_loss",
     "glm_sample_indices", "glm_sample_indices_noalloc", "glm_gram_lower",
+    "glm_storage_layout", "glm_storage_read",
     "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
     "glm_batch_choice", "glm_batch_destroy",
 ]
@@ -126,6 +127,9 @@ def load():
             "glm_sample_indices": ([u64, ctypes.c_uint32, i64, i64, i64, vp], i32),
             "glm_sample_indices_noalloc": ([u64, ctypes.c_uint32, i64, i64, i64, vp], i32),
             "glm_gram_lower": ([vp, i32, i64, i32, i64, i64, i64, vp, vp, i32, vp], i32),
+            "glm_storage_layout": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i64)], i32),
+            "glm_storage_read": ([vp, i64, i64, vp, vp, vp, vp], i32),
             "glm_batch_opts_default": ([ctypes.POINTER(glm_batch_opts)], None),
             "glm_batch_create": ([i32, ctypes.POINTER(glm_problem_desc),
                                   ctypes.POINTER(glm_batch_opts), ctypes.POINTER(vp)], i32),
@@ -241,6 +245,12 @@ def glm_sample_indices_noalloc(seed, problem, first_draw, count, m, out) -> None
     out: host int32 buffer (numpy array) of at least `count` entries;
     count <= GLM_SAMPLE_NOALLOC_MAX.
     """
+    if count > 0:
+        import numpy as np
+        if not isinstance(out, np.ndarray) or out.dtype != np.int32 or out.size < count \
+                or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous host int32 numpy array of at least "
+                             "count entries")
     _check(load().glm_sample_indices_noalloc(seed, problem, first_draw, count, m, _ptr(out)))
 
 
@@ -250,6 +260,22 @@ GLM_SAMPLE_NOALLOC_MAX = 1 << 20
 def glm_gram_lower(Y, dtype, nouter, s, b, n, ld, row_scale, G, impl=0, stream=None) -> None:
     _check(load().glm_gram_lower(_ptr(Y), dtype, nouter, s, b, n, ld, _ptr(row_scale),
                                  _ptr(G), impl, stream))
+
+
+def glm_storage_layout(h):
+    """(dtype, lda, lda8) of what the handle stores."""
+    dt, lda, lda8 = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().glm_storage_layout(h, ctypes.byref(dt), ctypes.byref(lda), ctypes.byref(lda8)))
+    return dt.value, lda.value, lda8.value
+
+
+def glm_storage_read(h, row0, rows, A_out=None, colscale_out=None, fp8_out=None,
+                     rowscale_out=None) -> None:
+    """Copy stored rows / scales into host numpy buffers (None: skipped); the
+    buffers must hold rows * lda storage elements, n floats, rows * lda8
+    bytes and rows floats."""
+    _check(load().glm_storage_read(h, row0, rows, _ptr(A_out), _ptr(colscale_out),
+                                   _ptr(fp8_out), _ptr(rowscale_out)))
 
 
 def glm_stream(h) -> int:

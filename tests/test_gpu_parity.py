@@ -97,6 +97,9 @@ def test_ca_fp32_matches_oracle_c1(G, c1, cluster):
     (1024, 300, 9, 5, 47, synth.LSQ, 5e-3),
     (4000, 18, 32, 8, 256, synth.LOGISTIC, 1e-4),   # SUSY-like width
     (4000, 28, 32, 8, 256, synth.LSQ, 0.0),         # HIGGS-like width
+    (300, 1, 4, 3, 40, synth.LOGISTIC, 1e-3),       # one column
+    (700, 3, 8, 5, 64, synth.LSQ, 0.0),             # three columns
+    (500, 1, 16, 4, 64, synth.LSQ, 1e-2),           # one column, 16 rows a block
 ])
 def test_ca_fp32_ragged_shapes(G, m, n, b, s, iters, loss, lam):
     pr = synth.ragged(m, n, seed=m + n, loss=loss, lam=lam)
@@ -318,8 +321,32 @@ def test_low_precision_final_loss(G, c1, storage, gram):
     ref = oracle.sgd(c1.A, c1.y, c1.loss, 16, 0.5, 1e-4, 2048, 0)
     f = oracle.loss(c1.A, c1.y, c1.loss, 1e-4, x)
     fr = oracle.loss(c1.A, c1.y, c1.loss, 1e-4, ref)
-    tol = 1e-3 if gram != "e4m3" else 5e-3
-    assert abs(f - fr) <= tol * fr, (storage, gram, f, fr)
+    assert abs(f - fr) <= 1e-3 * fr, (storage, gram, f, fr)
+
+
+@pytest.fixture(scope="module")
+def c3_small():
+    # the wide logistic workload's features (N(0,1) times log-uniform column
+    # scales in [0.1, 10], n = 2048, lambda = 1e-3) with m reduced to 65,536
+    return synth.logistic_wide(65536, 2048, seed=0, lam=1e-3)
+
+
+@pytest.mark.parametrize("storage,gram,s,rec", [
+    ("bf16", "e4m3", 16, -1), ("bf16", "bf16", 16, -1), ("f16", "e4m3", 16, -1),
+    ("f32", "f32", 16, -1), ("bf16", "e4m3", 32, 1), ("bf16", "e4m3", 32, 0),
+    ("bf16", "bf16", 64, 1), ("bf16", "bf16", 64, 0)])
+def test_wide_shape_final_loss(G, c3_small, storage, gram, s, rec):
+    # per-column-scaled BF16 / FP16 storage, FP8-E4M3 Gram with per-row
+    # scales vs BF16 vs FP32, b = 128; the FP64 recurrence on and off at
+    # s = 32, 64: final risk within 1e-3 of the FP64 oracle's
+    pr, lam, b, eta, T = c3_small, 1e-3, 128, 2.0 ** -10, 2048
+    ds = _ds(G, pr, storage, fp8_copy=(gram == "e4m3"))
+    x = _run(G, ds, pr, s, b, eta, lam, T, 0, gram_dtype=gram, recurrence_f64=rec)
+    ref = oracle.sgd(pr.A, pr.y, pr.loss, b, eta, lam, T, 0)
+    f = oracle.loss(pr.A, pr.y, pr.loss, lam, x)
+    fr = oracle.loss(pr.A, pr.y, pr.loss, lam, ref)
+    assert abs(f - fr) <= 1e-3 * fr, (storage, gram, s, rec, f, fr)
+    ds.close()
 
 
 # ----------------------------------------------------------------------------

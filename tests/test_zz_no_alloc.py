@@ -36,6 +36,26 @@ def test_noalloc_matches_allocating_path_twice(G, seed, problem, first, count, m
         assert np.array_equal(got, ref)
 
 
+def test_noalloc_matches_the_oracle(G):
+    import oracle
+    ref = oracle.sample_indices(13, 4, 2**33 + 7, 5000, 123_457)
+    for _ in range(2):
+        got = np.full(5000, -1, dtype=np.int32)
+        G.glm_sample_indices_noalloc(13, 4, 2**33 + 7, 5000, 123_457, got)
+        assert np.array_equal(got.astype(np.int64), ref)
+
+
+def test_noalloc_rejects_device_and_short_outputs(G):
+    # through the raw C entry point: the binding would refuse a torch tensor
+    dev = torch.zeros(16, dtype=torch.int32, device="cuda")
+    rc = G.load().glm_sample_indices_noalloc(0, 0, 0, 16, 10, dev.data_ptr())
+    assert rc == G.GLM_EINVAL and "host memory" in G.glm_last_error()
+    with pytest.raises(ValueError):
+        G.glm_sample_indices_noalloc(0, 0, 0, 16, 10, np.zeros(8, dtype=np.int32))
+    with pytest.raises(ValueError):
+        G.glm_sample_indices_noalloc(0, 0, 0, 4, 10, np.zeros(4, dtype=np.int64))
+
+
 def test_noalloc_smaller_call_after_larger(G):
     big = np.zeros(4096, dtype=np.int32)
     G.glm_sample_indices_noalloc(1, 0, 0, 4096, 1000, big)
