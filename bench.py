@@ -1,17 +1,27 @@
 """Benchmark: CA-SGD samples/s on one GB300 (and N independent replicas).
 
-Workload (default): binary logistic regression, dense A 1,048,576 x 512 FP32
-with entries N(0, 1/512), planted w*, 5% label flips; CA-SGD with s = 8,
-b = 64, eta = 0.5, lambda = 0, 65,536 SGD-equivalent iterations; Gram, margin
-and gradient operands in BF16 with FP32 accumulation, FP32 recurrence and
-master weights.  One bench step = one full training run (x reset to 0, then
-65,536 iterations through the C ABI, replayed as a CUDA graph).
+Workload (default, the headline): binary logistic regression, dense A
+1,048,576 x 512 FP32 with entries N(0, 1/512), planted w*, 5% label flips;
+CA-SGD with s = 8, b = 64, eta = 0.5, lambda = 0, 65,536 SGD-equivalent
+iterations; Gram, margin and gradient operands in BF16 with FP32
+accumulation, FP32 recurrence and master weights.  One bench step = one full
+training run (x reset to 0, then 65,536 iterations through the C ABI,
+replayed as a CUDA graph).
 
-Printed: one JSON line (rank 0) with the whole-job samples/s, the
-end-to-end number through the public API with host buffers, the roofline of
-the dominant kernel, the FP32 plain-SGD GPU baseline, the CPU oracle and, as
-an extra object, the batched workload (256 independent logistic / least-
-squares fits of uneven m, n and lambda, BF16 storage, autotuned s).
+Roofline (every line): the run's roofline time T_roof sums, over its outer
+iterations, the slower of the gathered bytes s b (n e_A + 4) at the measured
+HBM bandwidth and the strictly block-lower Gram flops b^2 s (s-1) n at the
+Gram type's peak; "step_frac" = T_roof / measured run time.  The dominant
+kernel's own roofline uses the same per-outer-iteration units (bytes for
+the gather and the chain, Gram flops for the Gram) over its average launch.
+
+Extra legs (skipped with --no-extras): the other s of the headline workload,
+TF32 and FP32 Grams, the FP32 plain-SGD GPU path, the end-to-end number with
+host buffers, the CPU oracle (one core and every core), time to target loss,
+the wide 400,000 x 2048 workload (per-column-scaled BF16/FP16 storage; FP8,
+BF16 and FP32 Grams; s = 16, 32, 64 with the FP64 recurrence on and off),
+the large 4,194,304 x 1024 BF16 least-squares workload (s = 64, b = 256)
+and the 256-problem batched workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU: one process per GPU (torchrun); each rank runs an independent
@@ -50,6 +60,8 @@ def _args():
     ap.add_argument("--gram", default="bf16", choices=["f32", "tf32", "bf16", "f16"])
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-wide", action="store_true", help="skip the 400,000 x 2048 legs")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4,194,304 x 1024 legs")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip SGD baseline, time-to-target, e2e and CPU legs")
     return ap.parse_args()
@@ -181,7 +193,10 @@ def _traffic(kernel: str, workload: str):
 
 def _cpu_baseline(pr, w, budget_s=15.0):
     """The FP64 oracle (plain SGD == CA-SGD iterate) on the host cores, on a
-    bounded sample of the same workload: the first T_s iterations."""
+    bounded sample of the same workload: the first T_s iterations, on one
+    core; then the same sample on every core at once (one independent index
+    stream per core, threads: the oracle's C call releases the GIL)."""
+    import concurrent.futures as cf
     import oracle
     oracle.build()
     T = 256
@@ -192,9 +207,20 @@ def _cpu_baseline(pr, w, budget_s=15.0):
     t0 = time.perf_counter()
     x = oracle.sgd(pr.A, pr.y, pr.loss, w["b"], w["eta"], w["lam"], Ts, w["seed"])
     dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    Tm = max(1, Ts // 3)   # a third of the sample per core keeps this leg ~5 s
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda k: oracle.sgd(pr.A, pr.y, pr.loss, w["b"], w["eta"], w["lam"], Tm,
+                                         w["seed"] + 1 + k), range(cores)))
+        dt_all = time.perf_counter() - t0
     return {"value": Ts * w["b"] / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
             "sample": f"first {Ts} of {w['iters']} iterations (b={w['b']}), FP64 SGD, "
-                      "single-threaded C", "seconds": dt, "iters": Ts}, x, Ts
+                      "single-threaded C", "seconds": dt, "iters": Ts,
+            "all_cores": {"value": cores * Tm * w["b"] / dt_all, "unit": "samples/s",
+                          "cores": cores, "seconds": dt_all,
+                          "sample": f"{cores} independent index streams of {Tm} iterations "
+                                    "each, one per host core (os.cpu_count)"}}, x, Ts
 
 
 def run_reference(args):
@@ -235,6 +261,140 @@ def _config(args, w):
             "gram_dtype": args.gram, "recurrence": "f32", "master_weights": "f32",
             "l2": "inputs larger than L2 (A is 2 GiB, rows gathered at random)",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+E_BYTES = {"f32": 4, "tf32": 4, "bf16": 2, "f16": 2, "e4m3": 1}
+
+
+def roofline(kms, kl, ms_run, T, s, b, n, e_A, gram, peaks, clocks, gram_impl=2,
+             workload=None):
+    """Roofline of one run: T_roof over the run (gathered bytes at HBM, Gram
+    flops at the Gram type's sustained peak, the slower per outer iteration)
+    against the measured run time, and the dominant kernel's own fraction
+    (same per-outer-iteration units over its average CUDA-event launch time;
+    the gather and the chain are held to the bytes, the Gram to its flops)."""
+    from paper_2606_18463_gb300 import accounting as acc
+    sm = (clocks or {}).get("sm_mhz") or 2070.0
+    simt = gram == "f32" or gram_impl in (1, 3)
+    p_tc = acc.gram_peak_tflops("f32" if simt else gram, peaks["bf16_sustained"], sm)
+    t_roof = acc.roof_seconds(T, s, b, n, e_A, peaks["hbm"], p_tc) * 1e3
+    by, fl = acc.run_bytes_flops(T, s, b, n, e_A)
+    names = ["gather", "gram", "chain"]
+    dom = max(range(3), key=lambda k: kms[k])
+    avg_ms = kms[dom] / max(kl[dom], 1)
+    frac_units = 1.0 / max(kl[dom], 1)          # share of the run one launch covers
+    if names[dom] == "gram":
+        p_burst = acc.gram_peak_tflops("f32" if simt else gram, peaks["bf16"], sm)
+        achieved = fl * frac_units / (avg_ms / 1e3) / 1e12
+        peak, unit = p_burst, "TFLOP/s"
+        bound = "alu" if simt else "tensor"
+        psrc = ("FP32 FMA: 152 SMs x 128 lanes x 2 flop x median SM clock" if simt else
+                f"{peaks['src']} bf16 burst x {acc.TC_RATIO[gram]} ({gram} nominal ratio)")
+    else:
+        achieved = by * frac_units / (avg_ms / 1e3) / 1e9
+        peak, unit, bound = peaks["hbm"], "GB/s", "hbm"
+        psrc = f"{peaks['src']} HBM copy"
+    kern = names[dom] if not (names[dom] == "gram" and simt) else "gram_simt"
+    return {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "peak_source": psrc,
+            "traffic": _traffic(kern, workload) if workload else None,
+            "avg_launch_ms": avg_ms, "launches_per_step": kl[dom],
+            "kernel_ms_per_step": {names[k]: kms[k] for k in range(3)},
+            "step_T_roof_ms": t_roof, "step_T_meas_ms": ms_run, "step_frac": t_roof / ms_run,
+            "step_bound": "tensor" if fl / (p_tc * 1e12) > by / (peaks["hbm"] * 1e9) else "hbm",
+            "units": "per outer iteration: B_Y = s b (n e_A + 4) bytes, "
+                     "F_G = b^2 s (s-1) n flops; e_A = %d" % e_A}
+
+
+def time_run(stream, torch, fn, reps=2):
+    """Median CUDA-event time (ms) of reps calls of fn after one warm-up."""
+    fn()
+    stream.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def leg(ds, stream, torch, glm, peaks, clocks, *, name, s, b, eta, lam, T, seed, e_A, gram,
+        n, x, reps=2, **opts):
+    """One timed configuration on an existing dataset handle."""
+    o = dict(opts, gram_dtype=gram, timing=1)
+
+    def run():
+        x.zero_()
+        ds.ca_sgd(x, s, b, eta, lam, T, seed, **o)
+    with torch.cuda.stream(stream):
+        ms = time_run(stream, torch, run, reps)
+    ds.sync()
+    kms, kl = glm.glm_kernel_times(ds.h)
+    plan = glm.glm_ca_plan(ds.h, s, b, eta, lam, T, glm.default_ca_opts(**o))
+    r = {"workload": name, "value": T * b / (ms / 1e3), "unit": "samples/s", "ms_per_run": ms,
+         "s": s, "b": b, "eta": eta, "lambda": lam, "iters": T, "gram_dtype": gram,
+         "recurrence": "f64" if plan.recurrence_f64 else "f32", "gram_impl": plan.gram_impl,
+         "cluster": plan.cluster, "launches_per_run": plan.launches,
+         "final_loss": ds.loss_value(x, lam)}
+    r["roofline"] = roofline(kms, kl, ms, T, s, b, n, e_A, gram, peaks, clocks,
+                             gram_impl=plan.gram_impl)
+    return r
+
+
+def wide_legs(args, torch, synth, glm, peaks, clocks):
+    """The wide logistic workload: 400,000 x 2048, N(0,1) features times
+    log-uniform column scales in [0.1, 10], lambda = 1e-3, b = 128, eta =
+    2^-10 (the largest of 2^-k giving the lowest loss in an FP32 sweep at
+    T = 16,384), T = 16,384; storage BF16 / FP16 with per-column scales."""
+    pr = synth.logistic_wide(400_000, 2048, seed=0, lam=1e-3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        A = torch.from_numpy(pr.A).cuda()
+        y = torch.from_numpy(pr.y).cuda()
+    stream.synchronize()
+    ds = {"bf16": glm.Dataset(A, y, pr.loss, "bf16", fp8_copy=True, stream=stream),
+          "f16": glm.Dataset(A, y, pr.loss, "f16", stream=stream)}
+    del A, y
+    x = torch.zeros(pr.n, dtype=torch.float32, device="cuda")
+    common = dict(b=128, eta=2.0 ** -10, lam=1e-3, T=16384, seed=0, n=2048, x=x)
+    out = []
+    for st, gram, s, rec in [("bf16", "bf16", 16, -1), ("bf16", "e4m3", 16, -1),
+                             ("bf16", "f32", 16, -1), ("f16", "f16", 16, -1),
+                             ("bf16", "bf16", 32, 1), ("bf16", "bf16", 32, 0),
+                             ("bf16", "bf16", 64, 1), ("bf16", "bf16", 64, 0)]:
+        r = leg(ds[st], stream, torch, glm, peaks, clocks, name=f"wide 400000x2048 {st} storage",
+                s=s, e_A=2, gram=gram, recurrence_f64=rec, reps=1, **common)
+        r["storage"] = st
+        out.append(r)
+    for d in ds.values():
+        d.close()
+    return out
+
+
+def large_legs(args, torch, synth, glm, peaks, clocks):
+    """The large least-squares workload: 4,194,304 x 1024, A ~ N(0, 1/1024)
+    rounded to BF16 (the BF16 values are the data, 8 GiB), y = A x* +
+    N(0, 0.01^2), lambda = 1e-5, s = 64, b = 256, BF16 Gram, T = 65,536,
+    eta = 50 (as the least-squares parity case at this shape)."""
+    A, y, _ = synth.lsq_bf16_device(4_194_304, 1024, seed=5)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    ds = glm.Dataset(A.view(torch.int16), y, synth.LSQ, "bf16", input_dtype="bf16",
+                     stream=stream)
+    del A, y
+    x = torch.zeros(1024, dtype=torch.float32, device="cuda")
+    out = []
+    for rec in (1, 0):
+        r = leg(ds, stream, torch, glm, peaks, clocks, name="large lsq 4194304x1024 bf16",
+                s=64, b=256, eta=50.0, lam=1e-5, T=65536, seed=0, e_A=2, gram="bf16", n=1024,
+                x=x, recurrence_f64=rec, reps=1)
+        out.append(r)
+    ds.close()
+    return out
 
 
 def main():
@@ -298,38 +458,10 @@ def main():
     ms = job_ms(ms, ws, "cuda")
     value = job_value(ws, T * b, ms)
 
-    # ---- roofline of the dominant kernel ------------------------------------
+    # ---- roofline (run and dominant kernel) -------------------------------
     peaks = _peaks()
-    names = ["gather", "gram", "chain"]
-    dom = max(range(3), key=lambda k: kms[k])
-    avg_ms = kms[dom] / max(kl[dom], 1)
-    H = (T + s - 1) // s
-    per_launch_outer = H / max(kl[dom], 1)
-    e_op = {"f32": 4, "tf32": 4, "bf16": 2, "f16": 2}[args.gram]
-    if names[dom] == "gram":
-        flops = acc.gram_flops(s, b, w["n"]) * per_launch_outer
-        achieved = flops / (avg_ms / 1e3) / 1e12
-        if args.gram == "f32":
-            peak, unit, bound = 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s", "alu"
-            psrc = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-        else:
-            ratio = 0.5 if args.gram == "tf32" else 1.0
-            peak, unit, bound = peaks["bf16"] * ratio, "TFLOP/s", "tensor"
-            psrc = f"{peaks['src']} bf16 burst" + (" x 0.5 (tf32 nominal ratio)" if ratio < 1 else "")
-    else:
-        if names[dom] == "gather":
-            byts = (acc.gathered_bytes(s, b, w["n"], 4) + acc.staged_bytes(s, b, w["n"], e_op)) * per_launch_outer
-        else:
-            byts = acc.chain_bytes(s, b, w["n"], e_op) * per_launch_outer
-        achieved = byts / (avg_ms / 1e3) / 1e9
-        peak, unit, bound = peaks["hbm"], "GB/s", "hbm"
-        psrc = f"{peaks['src']} HBM copy"
-    roof = {"kernel": names[dom], "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": unit, "frac": achieved / peak, "peak_source": psrc,
-            "traffic": _traffic(names[dom] if not (names[dom] == "gram" and plan.gram_impl == 1)
-                                else "gram_simt", "c2"),
-            "avg_launch_ms": avg_ms, "launches_per_step": kl[dom],
-            "kernel_ms_per_step": {names[k]: kms[k] for k in range(3)}}
+    roof = roofline(kms, kl, ms, T, s, b, w["n"], 4, args.gram, peaks, clocks,
+                    gram_impl=plan.gram_impl, workload="c2")
 
     out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -362,6 +494,14 @@ def main():
                 sweep[f"s={s2}"] = {"samples_per_s": T * b / (ms2 / 1e3), "ms_per_run": ms2,
                                     "recurrence": "f64" if s2 >= 32 else "f32"}
         out["s_sweep"] = sweep
+
+        # ---- TF32 and FP32 Grams of the headline workload ---------------------
+        xg = torch.zeros(pr.n, dtype=torch.float32, device="cuda")
+        out["gram_legs"] = [
+            leg(ds, stream, torch, glm, peaks, clocks, name="c2 " + g, s=s, b=b, eta=w["eta"],
+                lam=w["lam"], T=T, seed=seed, e_A=4, gram=g, n=w["n"], x=xg,
+                cluster=args.cluster)
+            for g in ("tf32", "f32")]
 
         # ---- FP32 plain-SGD GPU baseline (same data, same index stream) -------
         with torch.cuda.stream(stream):
@@ -400,7 +540,8 @@ def main():
             dt = time.perf_counter() - t0
         out["e2e"] = {"value": ws * T * b * args.steps / dt, "unit": "samples/s",
                       "h2d_bytes_per_step": 4 * pr.n, "d2h_bytes_per_step": 4 * pr.n + 8,
-                      "includes": "x0 H2D, run, x_T D2H, full-data loss D2H",
+                      "includes": "x0 H2D, run, x_T D2H, full-data loss D2H; the "
+                                  "one-time dataset upload (glm_create) is excluded",
                       "final_loss": loss_e2e}
 
         if rank == 0:
@@ -418,8 +559,14 @@ def main():
             out["time_to_target"].update({"target_loss": target, "oracle_loss": f_or,
                                           "oracle_iters": Ts})
     ds.close()
+    del pr
+    if not args.no_extras and ws == 1:
+        if not args.no_wide:
+            out["wide"] = wide_legs(args, torch, synth, glm, peaks, clocks)
+        if not args.no_large:
+            out["large"] = large_legs(args, torch, synth, glm, peaks, clocks)
     if not args.no_extras and not args.no_batch:
-        out["batched"] = _batched(args, torch, synth, glm, rank)
+        out["batched"] = _batched(args, torch, synth, glm, rank, peaks)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -429,7 +576,7 @@ def main():
 BATCH = {"P": 256, "b": 64, "iters": 4096, "eta": 0.25, "data_seed": 0}
 
 
-def _batched(args, torch, synth, glm, rank):
+def _batched(args, torch, synth, glm, rank, peaks):
     """The batched workload: 256 independent fits in one run (gather, grouped
     Gram and a persistent work-queue chain per round; all rounds one CUDA
     graph); m log-uniform in [4096, 131072], n cycling 64..1024, lambda on
@@ -473,8 +620,23 @@ def _batched(args, torch, synth, glm, rank):
         sp = str(bt.choice(p)[0])
         choice[str(n)][sp] = choice[str(n)].get(sp, 0) + 1
     losses = bt.loss(xs)
+    # roofline of the whole batch: every problem's gathered bytes (BF16
+    # storage) and strictly block-lower Gram flops at its chosen s; the
+    # problems share the GPU, so the bound is the slower of the two totals
+    from paper_2606_18463_gb300 import accounting as acc
+    tby = tfl = 0
+    for p, pr in enumerate(probs):
+        sp = bt.choice(p)[0]
+        by, fl = acc.run_bytes_flops(cfg["iters"], sp, cfg["b"], int(pr["A"].shape[1]), 2)
+        tby += by
+        tfl += fl
+    t_roof = max(tby / (peaks["hbm"] * 1e9), tfl / (peaks["bf16_sustained"] * 1e12)) * 1e3
     bt.close()
     return {"value": samples / (ms / 1e3), "unit": "samples/s", "ms_per_run": ms,
+            "roofline": {"step_T_roof_ms": t_roof, "step_T_meas_ms": ms,
+                         "step_frac": t_roof / ms, "gathered_bytes": tby, "gram_flops": tfl,
+                         "bound": "hbm" if tby / (peaks["hbm"] * 1e9) >=
+                         tfl / (peaks["bf16_sustained"] * 1e12) else "tensor"},
             "problems": cfg["P"], "rows_total": int(sum(p["A"].shape[0] for p in probs)),
             "iters_per_problem": cfg["iters"], "b": cfg["b"], "storage": "bf16",
             "autotuned_s_by_n": choice, "create_and_tune_s": t_create,

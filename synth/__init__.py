@@ -17,6 +17,9 @@ measured on:
                     [0.1, 10] (an epsilon-shaped 400000 x 2048 stand-in).
   lsq_planted       dense N(0, var) features, y = A x* + N(0, noise^2).
   lsq_bf16          as lsq_planted but the BF16-rounded values are the data.
+  lsq_bf16_device   the same recipe drawn with torch's CUDA generator, for
+                    sizes (4,194,304 x 1024) that a host generator makes slow;
+                    its bytes differ from lsq_bf16's (another stream).
   batch_problems    the 256-problem batch: log-uniform m, cycling n, lambda
                     on a log grid, alternating logistic / least squares.
 """
@@ -190,3 +193,26 @@ def ragged(m: int, n: int, seed: int = 0, loss: int = LOGISTIC,
     if loss == LOGISTIC:
         return logistic_planted(m, n, seed=seed, lam=lam)
     return lsq_planted(m, n, seed=seed, lam=lam)
+
+
+def lsq_bf16_device(m: int, n: int, seed: int = 0, noise: float = 0.01,
+                    chunk_rows: int = 1 << 18):
+    """Least squares whose data ARE BF16 values, drawn on the current CUDA
+    device: A_ij ~ N(0, 1/n) rounded to BF16, x* ~ N(0, I) (numpy PCG64),
+    y = A x* + N(0, noise^2) (FP64 products of the BF16 values, stored FP32).
+    Returns (A as a CUDA bfloat16 tensor, y as a CUDA float32 tensor, x*)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(np.random.default_rng([seed, 606, m, n]).integers(1 << 62)))
+    xs = np.random.default_rng([seed, 607, m, n]).standard_normal(n)
+    xd = torch.from_numpy(xs).cuda()
+    A = torch.empty((m, n), dtype=torch.bfloat16, device="cuda")
+    y = torch.empty(m, dtype=torch.float32, device="cuda")
+    for i in range(0, m, chunk_rows):
+        r = min(chunk_rows, m - i)
+        blk = torch.randn((r, n), generator=g, device="cuda", dtype=torch.float32)
+        blk.mul_(1.0 / math.sqrt(n))
+        A[i:i + r] = blk.to(torch.bfloat16)
+        e = torch.randn(r, generator=g, device="cuda", dtype=torch.float64)
+        y[i:i + r] = (A[i:i + r].double() @ xd + noise * e).float()
+    return A, y, xs
