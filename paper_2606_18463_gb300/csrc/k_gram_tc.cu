@@ -2,13 +2,17 @@
 // the 5th-generation tensor cores (paper Algorithm 1, Gram step; Sec. 5.2's
 // G_L is the only part the recurrence reads).
 //
-// One persistent CTA per SM walks a static list of 128 x 128 output tiles of
-// the lower triangle of every outer iteration's (s b) x (s b) Gram; tiles
-// holding no strictly-lower block entry are skipped.  Warp roles:
-//   warp 0      TMA producer: both operand tiles (rows of Y, K-major, 128-byte
-//               swizzle) per 128-byte K chunk into a STAGES-deep ring;
-//   warp 1      allocates 256 TMEM columns (two 128-column FP32 accumulators)
-//               and one elected lane issues tcgen05.mma (M=128, N=128), four
+// One persistent CTA per SM walks a static list of 128 x N output tiles
+// (N = 256, or 128 when the wide tiles would leave SMs idle) of the lower
+// triangle of every outer iteration's (s b) x (s b) Gram; tiles holding no
+// strictly-lower block entry are skipped.  A 128 x 256 tile reads 1.5 times
+// fewer operand bytes per flop than a 128 x 128 one, which is what keeps the
+// SMs' operand stream from L2 below the tensor cores' rate.  Warp roles:
+//   warp 0      TMA producer: the tile's 128 A rows and N B rows of Y
+//               (K-major, 128-byte swizzle) per 128-byte K chunk into a
+//               STAGES-deep ring;
+//   warp 1      allocates 2N TMEM columns (two N-column FP32 accumulators)
+//               and one elected lane issues tcgen05.mma (M=128, N), four
 //               MMAs per K chunk, committing each stage back to the producer
 //               and each finished accumulator to the epilogue;
 //   warps 2..5  epilogue: tcgen05.ld 32x32b rows out of TMEM, per-row scales
@@ -24,12 +28,18 @@ namespace glm {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kTile = 128;                 // M = N = 128
+constexpr int kTile = 128;                 // M (rows of a tile)
 constexpr int kChunkBytes = 128;           // K bytes per stage row (one SW128 atom)
-constexpr int kOperandBytes = kTile * kChunkBytes;  // 16 KB per operand per stage
+constexpr int kOperandBytes = kTile * kChunkBytes;  // 16 KB per 128 rows per stage
 constexpr int kThreads = 192;
 constexpr long long kBudget = 4000000000ll;
-constexpr uint32_t kTmemCols = 256;
+
+template <int kN> struct TileCfg {
+  static constexpr int kBBytes = kN * kChunkBytes;             // B rows per stage
+  static constexpr int kStageBytes = kOperandBytes + kBBytes;  // A + B
+  static constexpr uint32_t kTmemCols = 2 * kN;                // two accumulators
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 8 * (2 * kStages + 6) + 32;
+};
 
 struct TcArgs {
   CUtensorMap ymap;       // 2D (ld, rows) map, box (128 bytes of K, 128 rows), SW128
@@ -112,47 +122,64 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: D FP32, A/B K-major, M = N = 128.
-template <int DT> __host__ __device__ constexpr uint32_t instr_desc() {
+// Instruction descriptor: D FP32, A/B K-major, M = 128, N = kN.
+template <int DT, int kN> __host__ __device__ constexpr uint32_t instr_desc() {
   // operand format field: kind::f16 -> F16 0 / BF16 1; kind::tf32 -> 2;
   // kind::f8f6f4 -> E4M3 0
   return (1u << 4)                                                      // D = F32
          | ((uint32_t)(DT == GLM_BF16 ? 1 : DT == GLM_TF32 ? 2 : 0) << 7)  // A format
          | ((uint32_t)(DT == GLM_BF16 ? 1 : DT == GLM_TF32 ? 2 : 0) << 10) // B format
-         | ((uint32_t)(kTile >> 3) << 17)                               // N >> 3
+         | ((uint32_t)(kN >> 3) << 17)                                  // N >> 3
          | ((uint32_t)(kTile >> 4) << 24);                              // M >> 4
 }
 
-// Output tile t of the flattened (outer step, lower-triangular tile pair)
-// list; returns false when the tile holds no strictly-lower block entry.
+// Lower-triangular tiles of one outer iteration: row tiles tj of 128 rows,
+// column panels ti of kN rows of Y with ti * kN <= tj * 128 + 127.  With
+// q = kN / 128 row tiles per panel, row tile tj has tj / q + 1 panels, so the
+// q row tiles of group k = tj / q hold q (k + 1) tiles and the groups before
+// group k hold q k (k + 1) / 2.
+template <int kN> __host__ __device__ inline int64_t tiles_per_outer(int64_t sb) {
+  constexpr int64_t q = kN / kTile;
+  const int64_t T = (sb + kTile - 1) / kTile;   // row tiles
+  int64_t P = 0;
+  for (int64_t k = 0; k * q < T; ++k) P += min(q, T - k * q) * (k + 1);
+  return P;
+}
+
+// Output tile t of the flattened (outer step, lower-triangular tile) list;
+// returns false when the tile holds no strictly-lower block entry.
 struct Tile {
   int64_t g, tj, ti, rows_g;
 };
-__device__ __forceinline__ bool tile_at(const TcArgs &a, int64_t T, int64_t P, int64_t t,
-                                        Tile &o) {
+template <int kN>
+__device__ __forceinline__ bool tile_at(const TcArgs &a, int64_t P, int64_t t, Tile &o) {
+  constexpr int64_t q = kN / kTile;
   const int64_t sb = (int64_t)a.s * a.b;
   o.g = t / P;
   const int64_t p = t - o.g * P;
-  int64_t tj = (int64_t)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-  while (tj * (tj + 1) / 2 > p) --tj;
-  while ((tj + 1) * (tj + 2) / 2 <= p) ++tj;
-  o.tj = tj;
-  o.ti = p - tj * (tj + 1) / 2;
+  // group k: the largest k with q k (k + 1) / 2 <= p
+  int64_t k = (int64_t)((sqrt(8.0 * (double)p / (double)q + 1.0) - 1.0) * 0.5);
+  while (k > 0 && q * k * (k + 1) / 2 > p) --k;
+  while (q * (k + 1) * (k + 2) / 2 <= p) ++k;
+  const int64_t rem = p - q * k * (k + 1) / 2;   // < q (k + 1)
+  o.tj = k * q + rem / (k + 1);
+  o.ti = rem % (k + 1);
   o.rows_g = min(sb, a.rows - o.g * sb);
-  const int64_t r0 = o.tj * kTile, c0 = o.ti * kTile;
+  const int64_t r0 = o.tj * kTile, c0 = o.ti * kN;
   const int64_t r_last = min(r0 + kTile, o.rows_g) - 1;
   return r_last >= r0 && r_last / a.b > c0 / a.b;
 }
 
-template <int DT>
+template <int DT, int kN>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const __grid_constant__ TcArgs a) {
+  using Cfg = TileCfg<kN>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t sbase0 = smem_u32(smem_raw);
   unsigned char *smem = smem_raw + (round_up(sbase0, 1024) - sbase0);
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t stage_a = sbase;                                  // + st * 32 KB
-  const uint32_t bars = sbase + kStages * 2 * kOperandBytes;       // 8-byte barriers
+  const uint32_t stage_a = sbase;                                  // + st * kStageBytes
+  const uint32_t bars = sbase + kStages * Cfg::kStageBytes;        // 8-byte barriers
   const uint32_t full0 = bars, empty0 = bars + 8 * kStages;
   const uint32_t tfull0 = bars + 16 * kStages, tempty0 = tfull0 + 16;
   const uint32_t drain = tempty0 + 16;        // MMA unwind barrier
@@ -174,7 +201,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
     s_abort = 0;
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_alloc(tmem_slot, Cfg::kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -183,8 +210,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem + (tmem_slot - sbase));
 
   const int64_t sb = (int64_t)a.s * a.b;
-  const int64_t T = (sb + kTile - 1) / kTile;
-  const int64_t P = T * (T + 1) / 2;
+  const int64_t P = tiles_per_outer<kN>(sb);
   const int64_t ntiles = a.nouter * P;
   volatile int *vabort = &s_abort;
 
@@ -194,9 +220,9 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
       int64_t it = 0;
       for (int64_t t = blockIdx.x; t < ntiles && !*vabort; t += gridDim.x) {
         Tile tl;
-        if (!tile_at(a, T, P, t, tl)) continue;
+        if (!tile_at<kN>(a, P, t, tl)) continue;
         const int32_t ya = (int32_t)(tl.g * sb + tl.tj * kTile);
-        const int32_t yb = (int32_t)(tl.g * sb + tl.ti * kTile);
+        const int32_t yb = (int32_t)(tl.g * sb + tl.ti * kN);
         for (int kc = 0; kc < a.nk; ++kc, ++it) {
           const int st = (int)(it % kStages);
           if (it >= kStages &&
@@ -205,11 +231,14 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
             break;
           }
           const uint32_t full = full0 + 8 * st;
-          mbar_arrive_expect_tx(full, 2 * kOperandBytes);
+          mbar_arrive_expect_tx(full, Cfg::kStageBytes);
           const int32_t xk = kc * (kChunkBytes / elem_bytes(DT));
-          const uint32_t dA = stage_a + st * 2 * kOperandBytes;
+          const uint32_t dA = stage_a + st * Cfg::kStageBytes;
           tma_load_2d(dA, &a.ymap, xk, ya, full);
-          tma_load_2d(dA + kOperandBytes, &a.ymap, xk, yb, full);
+#pragma unroll
+          for (int h = 0; h < kN / kTile; ++h)  // B: kN rows in boxes of 128
+            tma_load_2d(dA + kOperandBytes + h * kOperandBytes, &a.ymap, xk, yb + h * kTile,
+                        full);
         }
       }
       // unwind: wait (bounded) for the loads still in flight
@@ -220,11 +249,11 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      constexpr uint32_t idesc = instr_desc<DT>();
+      constexpr uint32_t idesc = instr_desc<DT, kN>();
       int64_t it = 0, tc = 0;
       for (int64_t t = blockIdx.x; t < ntiles && !*vabort; t += gridDim.x) {
         Tile tl;
-        if (!tile_at(a, T, P, t, tl)) continue;
+        if (!tile_at<kN>(a, P, t, tl)) continue;
         const int buf = (int)(tc & 1);
         if (tc >= 2 &&
             !mbar_wait_bounded(tempty0 + 8 * buf, (uint32_t)((tc / 2 - 1) & 1), kBudget)) {
@@ -232,7 +261,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
           break;
         }
         tc_fence_after();
-        const uint32_t tmem_d = tmem_base + (uint32_t)(buf * kTile);
+        const uint32_t tmem_d = tmem_base + (uint32_t)(buf * kN);
         bool ok = true;
         for (int kc = 0; kc < a.nk; ++kc, ++it) {
           const int st = (int)(it % kStages);
@@ -242,7 +271,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
             break;
           }
           tc_fence_after();
-          const uint32_t sa = stage_a + st * 2 * kOperandBytes;
+          const uint32_t sa = stage_a + st * Cfg::kStageBytes;
           const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + kOperandBytes);
 #pragma unroll
           for (int k = 0; k < kChunkBytes / 32; ++k)  // 32 bytes of K per MMA
@@ -265,7 +294,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
     int64_t tc = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       Tile tl;
-      if (!tile_at(a, T, P, t, tl)) continue;
+      if (!tile_at<kN>(a, P, t, tl)) continue;
       const int buf = (int)(tc & 1);
       if (!mbar_wait_bounded(tfull0 + 8 * buf, (uint32_t)((tc / 2) & 1), kBudget)) {
         atomicOr(&s_abort, 1);
@@ -279,11 +308,11 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
       float *grow = a.G + tl.g * gram_size(a.s, a.b) + gram_off(j, a.b) + l * gram_ld(j, a.b);
       const float srow = (DT == GLM_E4M3 && row_ok) ? a.rs[tl.g * sb + rho] : 1.f;
 #pragma unroll 1
-      for (int cc = 0; cc < kTile / 32; ++cc) {
+      for (int cc = 0; cc < kN / 32; ++cc) {
         float v[32];
-        tmem_ld32(tmem_base + (uint32_t)(buf * kTile + cc * 32) + ((uint32_t)(quad * 32) << 16),
+        tmem_ld32(tmem_base + (uint32_t)(buf * kN + cc * 32) + ((uint32_t)(quad * 32) << 16),
                   v);
-        const int64_t c0 = tl.ti * kTile + cc * 32;
+        const int64_t c0 = tl.ti * kN + cc * 32;
         if (!row_ok || c0 >= limit) continue;
         if (DT == GLM_E4M3) {
 #pragma unroll
@@ -311,8 +340,25 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
   if (s_abort && threadIdx.x == 0 && a.flag) atomicOr(a.flag, FLAG_TIMEOUT);
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, kTmemCols);
+    tmem_dealloc(tmem_base, Cfg::kTmemCols);
   }
+}
+
+template <int kN>
+int launch_n(const TcArgs &a, int sms, int64_t ntiles, cudaStream_t st) {
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  const size_t smem = TileCfg<kN>::kSmem;
+  void (*kern)(TcArgs);
+  switch (a.dt) {
+  case GLM_BF16: kern = k_gram_tc<GLM_BF16, kN>; break;
+  case GLM_F16: kern = k_gram_tc<GLM_F16, kN>; break;
+  case GLM_TF32: kern = k_gram_tc<GLM_TF32, kN>; break;
+  default: kern = k_gram_tc<GLM_E4M3, kN>; break;
+  }
+  GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, kThreads, smem, st>>>(a);
+  GLM_CUDA_TRY(cudaGetLastError());
+  return GLM_OK;
 }
 
 }  // namespace
@@ -345,24 +391,13 @@ int launch_gram_tc(const GramArgs &g, cudaStream_t st) {
   a.dt = g.dt;
   a.nk = (int)((g.n * eb + kChunkBytes - 1) / kChunkBytes);  // K chunks covering n
   const int64_t sb = (int64_t)g.s * g.b;
-  const int64_t T = (sb + kTile - 1) / kTile;
-  const int64_t ntiles = g.nouter * T * (T + 1) / 2;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)(ntiles < sms ? ntiles : sms);
-  const size_t smem = 1024 + kStages * 2 * kOperandBytes + 8 * (2 * kStages + 6) + 32;
-  void (*kern)(TcArgs);
-  switch (g.dt) {
-  case GLM_BF16: kern = k_gram_tc<GLM_BF16>; break;
-  case GLM_F16: kern = k_gram_tc<GLM_F16>; break;
-  case GLM_TF32: kern = k_gram_tc<GLM_TF32>; break;
-  default: kern = k_gram_tc<GLM_E4M3>; break;
-  }
-  GLM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, kThreads, smem, st>>>(a);
-  GLM_CUDA_TRY(cudaGetLastError());
-  return GLM_OK;
+  // wide tiles unless they would leave SMs idle (few, long-K tiles)
+  const int64_t wide = g.nouter * tiles_per_outer<256>(sb);
+  if (wide >= sms) return launch_n<256>(a, sms, wide, st);
+  return launch_n<128>(a, sms, g.nouter * tiles_per_outer<128>(sb), st);
 }
 
 }  // namespace glm

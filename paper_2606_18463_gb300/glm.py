@@ -245,7 +245,7 @@ def glm_sample_indices_noalloc(seed, problem, first_draw, count, m, out) -> None
     out: host int32 buffer (numpy array) of at least `count` entries;
     count <= GLM_SAMPLE_NOALLOC_MAX.
     """
-    if count > 0:
+    if 0 < count <= GLM_SAMPLE_NOALLOC_MAX:   # larger counts: the C call rejects them
         import numpy as np
         if not isinstance(out, np.ndarray) or out.dtype != np.int32 or out.size < count \
                 or not out.flags["C_CONTIGUOUS"]:
