@@ -144,6 +144,15 @@ typedef struct {
                          else GLM_EINVAL; never chosen automatically).       */
   int timing;         /* 1: record CUDA events around every kernel of the run
                          (read back with glm_kernel_times).  Default 0.       */
+  int64_t wait_probe_cycles;
+                      /* Failure-path test hook; 0 (default) = off.  When > 0,
+                         one thread of every CTA of the chain and tcgen05
+                         Gram kernels first waits, for at most this many SM
+                         cycles, on a barrier that nothing signals; the wait
+                         gives up, and the kernels unwind as after any device
+                         timeout before any data moves between CTAs (copies
+                         in flight are drained, TMEM is freed, x is left as
+                         it was).  glm_sync then returns GLM_ETIMEOUT.      */
 } glm_ca_opts;
 
 void glm_ca_opts_default(glm_ca_opts *o);
@@ -265,6 +274,15 @@ int glm_sample_indices_noalloc(uint64_t seed, uint32_t problem, int64_t first_dr
 /* ---- kernel-level entry points (tests, micro-benchmarks) ----------------- */
 
 /*
+ * Failure-path test hook (host side): the next `after` device allocations the
+ * library makes succeed and the one after them fails as if the device were
+ * out of memory, so the call making it returns GLM_ENOMEM after releasing
+ * what it had allocated.  A negative value disarms the hook (the default).
+ * Affects every thread of the process.
+ */
+void glm_debug_fail_alloc(int64_t after);
+
+/*
  * Layout of the dataset a handle stores (Table 1 slot u_A, created by
  * glm_create_ex): *dtype = GLM_F32, GLM_BF16 or GLM_F16; *lda = row stride in
  * elements (n rounded up to a multiple of 8; columns n..lda-1 hold zeros);
@@ -340,6 +358,9 @@ typedef struct {
   int input_dtype;    /* GLM_F32 (default) or GLM_BF16                      */
   int input_on_host;  /* 1 (default): descriptors point to host memory      */
   void *stream;       /* as glm_create_opts.stream                          */
+  int64_t wait_probe_cycles; /* as glm_ca_opts.wait_probe_cycles, for the
+                         batch's tcgen05 Gram launches (glm_batch_run then
+                         returns GLM_ETIMEOUT); 0 (default) = off            */
 } glm_batch_opts;
 
 void glm_batch_opts_default(glm_batch_opts *o);
@@ -365,7 +386,9 @@ int glm_batch_create(int P, const glm_problem_desc *descs,
  * CUDA graph and replayed by later runs.  xs: host array of P device FP32[n_p]
  * pointers, read as x0 and written with x_T.  status: host int[P] or NULL,
  * filled with GLM_OK or GLM_ENONFINITE per problem (flags are then cleared).
- * Blocks.
+ * If a Gram launch gave up a bounded device wait, every entry is
+ * GLM_ETIMEOUT and so is the return value (the iterates are then not
+ * meaningful).  Blocks.
  */
 int glm_batch_run(glm_batch bt, float *const *xs, int *status);
 

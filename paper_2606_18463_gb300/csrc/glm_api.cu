@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -28,10 +29,27 @@ int cuda_error(cudaError_t e, const char *what) {
   return e == cudaErrorMemoryAllocation ? GLM_ENOMEM : GLM_ECUDA;
 }
 
+// glm_debug_fail_alloc: allocations left before an injected failure (< 0: off)
+static std::atomic<int64_t> g_alloc_countdown{-1};
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  int64_t c = g_alloc_countdown.load();
+  while (c >= 0) {
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+      if (c == 0) {  // this allocation is the injected failure
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 int DevBuf::ensure(size_t need) {
   if (need <= bytes && ptr) return GLM_OK;
   release();
-  cudaError_t e = cudaMalloc(&ptr, need ? need : 16);
+  cudaError_t e = dev_malloc(&ptr, need ? need : 16);
   if (e != cudaSuccess) {
     ptr = nullptr;
     bytes = 0;
@@ -52,7 +70,7 @@ bool RunKey::operator==(const RunKey &o) const {
          kahan == o.kahan && cluster == o.cluster && gram_impl == o.gram_impl &&
          sgd == o.sgd && b == o.b && iters == o.iters && first_iter == o.first_iter &&
          chunk == o.chunk && seed == o.seed && problem == o.problem && eta == o.eta &&
-         lambda == o.lambda && x == o.x && timing == o.timing;
+         lambda == o.lambda && x == o.x && timing == o.timing && probe == o.probe;
 }
 
 int loss_partials_needed();
@@ -109,6 +127,7 @@ struct RunPlan {
   uint64_t seed = 0;
   uint32_t problem = 0;
   int64_t first_iter = 0;
+  int64_t probe = 0;
   float *x = nullptr;
 };
 
@@ -144,6 +163,8 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   p.kahan = o->kahan ? 1 : 0;
   p.use_graph = o->use_graph ? 1 : 0;
   p.timing = o->timing ? 1 : 0;
+  if (o->wait_probe_cycles < 0) return set_error(GLM_EINVAL, "wait_probe_cycles must be >= 0");
+  p.probe = o->wait_probe_cycles;
   // precision slots
   int gdt = o->gram_dtype < 0 ? h->dtype : o->gram_dtype;
   if (sgd) gdt = (o->gram_dtype < 0) ? GLM_F32 : o->gram_dtype;
@@ -289,6 +310,7 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
   ca.cluster = p.cluster;
   ca.sbp = round_up(sb, 4);
   ca.prefetch = 1;
+  ca.probe = p.probe;
   double cp = 1.0;
   for (int j = 0; j <= p.s; ++j) {
     ca.cpow[j] = cp;
@@ -357,6 +379,7 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
       gr.n = h->n;
       gr.G = static_cast<float *>(h->gbuf[buf].ptr);
       gr.flag = h->dflag;
+      gr.probe = p.probe;
       GLM_TRY(tmark(h, p, side, ci, 1, 0));
       if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, side));
       else if (p.gram_impl == 3) GLM_TRY(launch_gram_simt_f16acc(gr, side));
@@ -390,7 +413,7 @@ int run_common(Handle *h, int s, int64_t b, float eta, float lambda, int64_t ite
   key.kahan = p.kahan; key.cluster = p.cluster; key.gram_impl = p.gram_impl; key.sgd = p.sgd;
   key.b = p.b; key.iters = p.iters; key.first_iter = p.first_iter; key.chunk = p.chunk;
   key.seed = p.seed; key.problem = p.problem; key.eta = p.eta; key.lambda = p.lambda;
-  key.x = p.x; key.timing = p.timing;
+  key.x = p.x; key.timing = p.timing; key.probe = p.probe;
   if (realloc && h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -461,7 +484,10 @@ void glm_ca_opts_default(glm_ca_opts *o) {
   o->chunk_outer = 0;
   o->gram_impl = 0;
   o->timing = 0;
+  o->wait_probe_cycles = 0;
 }
+
+void glm_debug_fail_alloc(int64_t after) { g_alloc_countdown.store(after < 0 ? -1 : after); }
 
 int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss, int dtype,
                   const glm_create_opts *opts, glm_handle *out) {
@@ -518,30 +544,30 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
   cudaStream_t st = h->stream;
   const int ieb = opts->input_dtype == GLM_BF16 ? 2 : 4;
   const int eb = elem_bytes(dtype);
-  CK(cudaMalloc(&h->A, (size_t)m * h->lda * eb));
-  CK(cudaMalloc(&h->y, (size_t)m * 4));
-  CK(cudaMalloc(&h->dflag, 16));
+  CK(dev_malloc(&h->A, (size_t)m * h->lda * eb));
+  CK(dev_malloc((void **)&h->y, (size_t)m * 4));
+  CK(dev_malloc((void **)&h->dflag, 16));
   CK(cudaMemsetAsync(h->dflag, 0, 16, st));
-  CK(cudaMalloc(&h->loss_partials, (size_t)loss_partials_needed() * 8));
-  CK(cudaMalloc(&h->loss_out, 8));
+  CK(dev_malloc((void **)&h->loss_partials, (size_t)loss_partials_needed() * 8));
+  CK(dev_malloc((void **)&h->loss_out, 8));
   // input in device memory (temporary upload when it lives on the host)
   const void *src = A;
   const float *ysrc = y;
   const bool host_in = opts->input_on_host || !is_device_ptr(A);
   if (host_in) {
-    CK(cudaMalloc(&tmpA, (size_t)m * n * ieb));
+    CK(dev_malloc(&tmpA, (size_t)m * n * ieb));
     CK(cudaMemcpyAsync(tmpA, A, (size_t)m * n * ieb, cudaMemcpyHostToDevice, st));
     src = tmpA;
   }
   if (opts->input_on_host || !is_device_ptr(y)) {
-    CK(cudaMalloc(&tmpy, (size_t)m * 4));
+    CK(dev_malloc((void **)&tmpy, (size_t)m * 4));
     CK(cudaMemcpyAsync(tmpy, y, (size_t)m * 4, cudaMemcpyHostToDevice, st));
     ysrc = tmpy;
   }
   CK(cudaMemcpyAsync(h->y, ysrc, (size_t)m * 4, cudaMemcpyDeviceToDevice, st));
   // per-column power-of-two scales (BF16 / F16 storage)
   if (dtype != GLM_F32 && opts->column_scales) {
-    CK(cudaMalloc(&acc, (size_t)n * 8));
+    CK(dev_malloc((void **)&acc, (size_t)n * 8));
     CK(cudaMemsetAsync(acc, 0, (size_t)n * 8, st));
     rc = launch_colsumsq(src, opts->input_dtype, m, n, acc, st);
     if (rc != GLM_OK) return fail(rc);
@@ -555,7 +581,7 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
       const double rms = sqrt(hs[k] / (double)m);
       kappa[k] = rms > 0.0 ? (float)ldexp(1.0, (int)nearbyint(log2(rms))) : 1.0f;
     }
-    CK(cudaMalloc(&h->colscale, (size_t)h->lda * 4));
+    CK(dev_malloc((void **)&h->colscale, (size_t)h->lda * 4));
     CK(cudaMemcpyAsync(h->colscale, kappa.data(), (size_t)h->lda * 4, cudaMemcpyHostToDevice,
                        st));
     CK(cudaStreamSynchronize(st));
@@ -564,8 +590,8 @@ int glm_create_ex(const void *A, const float *y, int64_t m, int64_t n, int loss,
   if (rc != GLM_OK) return fail(rc);
   if (opts->fp8_copy) {
     h->lda8 = round_up(n, 16);
-    CK(cudaMalloc(&h->A8, (size_t)m * h->lda8));
-    CK(cudaMalloc(&h->rowscale8, (size_t)m * 4));
+    CK(dev_malloc((void **)&h->A8, (size_t)m * h->lda8));
+    CK(dev_malloc((void **)&h->rowscale8, (size_t)m * 4));
     rc = launch_fp8_copy(h, src, opts->input_dtype, 0, m, st);
     if (rc != GLM_OK) return fail(rc);
   }
@@ -755,7 +781,7 @@ int glm_sample_indices(uint64_t seed, uint32_t problem, int64_t first_draw, int6
     return GLM_OK;
   }
   int32_t *d = nullptr;
-  GLM_CUDA_TRY(cudaMalloc(&d, (size_t)count * 4));
+  GLM_CUDA_TRY(dev_malloc((void **)&d, (size_t)count * 4));
   int rc = launch_sample(seed, problem, first_draw, count, m, d, 0);
   if (rc == GLM_OK) {
     cudaError_t e = cudaMemcpy(out, d, (size_t)count * 4, cudaMemcpyDeviceToHost);
@@ -832,6 +858,7 @@ int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b, i
   a.n = n;
   a.G = G;
   a.flag = nullptr;
+  a.probe = 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (impl == 0) impl = gram_tc_supported(dtype, ld) ? 2 : 1;
   if (impl == 2) {

@@ -88,6 +88,9 @@ struct Batch {
   bool planned = false;
   cudaGraphExec_t graph = nullptr;
   std::vector<float *> xs;  // iterate pointers the table holds
+  unsigned *bflag = nullptr;  // [0]: the Gram launches' flag word, [1]: the
+                              // tuner's scratch runs' flag word (every item)
+  int64_t probe = 0;          // glm_batch_opts.wait_probe_cycles
 };
 
 namespace {
@@ -242,6 +245,8 @@ int enqueue(Batch &B, const Plan &pl, cudaStream_t st) {
       ga.b = g.b;
       ga.n = g.n;
       ga.G = reinterpret_cast<float *>(gb + reinterpret_cast<size_t>(g.G));
+      ga.flag = B.bflag;
+      ga.probe = B.probe;
       const bool tc = B.gram_impl == 2 || (B.gram_impl == 0 && gram_tc_supported(B.gdt, g.ld));
       if (tc) GLM_TRY(launch_gram_tc(ga, st));
       else GLM_TRY(launch_gram_simt(ga, st));
@@ -275,6 +280,9 @@ int time_candidate(Batch &B, const std::vector<int> &sel, int s, float *xscratch
   make_plan(B, sel, iters, pl);
   std::vector<BatchItem> items;
   int rc = bind(B, pl, xp, &kmap, items);
+  // scratch runs raise their flags in a word of their own, never in a
+  // problem's flag word (which a user run may have set)
+  for (auto &it : items) it.flag = B.bflag + 1;
   if (rc == GLM_OK) rc = upload(B, pl, items);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (rc == GLM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
@@ -305,7 +313,7 @@ int autotune(Batch &B) {
   size_t xcount = 0;
   for (auto &kv : by_n) xcount = std::max(xcount, std::min<size_t>(kv.second.size(), 32) *
                                                       (size_t)round_up(kv.first, 8));
-  GLM_CUDA_TRY(cudaMalloc(&xs, xcount * 4));
+  GLM_CUDA_TRY(dev_malloc((void **)&xs, xcount * 4));
   int rc = GLM_OK;
   for (auto &kv : by_n) {
     std::vector<int> sel(kv.second.begin(),
@@ -326,12 +334,9 @@ int autotune(Batch &B) {
     if (rc != GLM_OK) break;
     for (int p : kv.second) B.pr[p].s = best;
   }
-  cudaStreamSynchronize(B.stream);
-  for (int p = 0; p < B.P; ++p) {  // the scratch runs may have raised flags
-    unsigned zero = 0;
-    cudaMemcpyAsync(reinterpret_cast<Handle *>(B.pr[p].h)->dflag, &zero, 4,
-                    cudaMemcpyHostToDevice, B.stream);
-  }
+  // the scratch runs' flags (a diverging candidate, a timed-out Gram) say
+  // nothing about the problems' own runs: clear both words
+  cudaMemsetAsync(B.bflag, 0, 2 * sizeof(unsigned), B.stream);
   cudaStreamSynchronize(B.stream);
   cudaFree(xs);
   return rc;
@@ -355,6 +360,7 @@ void glm_batch_opts_default(glm_batch_opts *o) {
   o->input_dtype = GLM_F32;
   o->input_on_host = 1;
   o->stream = nullptr;
+  o->wait_probe_cycles = 0;
 }
 
 int glm_batch_destroy(glm_batch bt) {
@@ -366,6 +372,7 @@ int glm_batch_destroy(glm_batch bt) {
     if (p.h) glm_destroy(p.h);
   B->ybuf.release(); B->labbuf.release(); B->gbuf.release();
   B->itembuf.release(); B->orderbuf.release(); B->queuebuf.release();
+  if (B->bflag) cudaFree(B->bflag);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
   return GLM_OK;
@@ -382,6 +389,7 @@ int glm_batch_create(int P, const glm_problem_desc *descs, const glm_batch_opts 
   if (!opts) opts = &dflt;
   if (opts->dtype != GLM_F32 && opts->dtype != GLM_BF16 && opts->dtype != GLM_F16)
     return set_error(GLM_EINVAL, "batch storage dtype must be F32, BF16 or F16");
+  if (opts->wait_probe_cycles < 0) return set_error(GLM_EINVAL, "wait_probe_cycles must be >= 0");
   int gdt = -1;
   for (int p = 0; p < P; ++p) {
     const glm_problem_desc &d = descs[p];
@@ -422,6 +430,13 @@ int glm_batch_create(int P, const glm_problem_desc *descs, const glm_batch_opts 
       return set_error(GLM_ECUDA, "cudaStreamCreateWithFlags");
     }
     B->own_stream = true;
+  }
+  B->probe = opts->wait_probe_cycles;
+  if (dev_malloc((void **)&B->bflag, 4 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemsetAsync(B->bflag, 0, 4 * sizeof(unsigned), B->stream) != cudaSuccess) {
+    cudaGetLastError();
+    glm_batch_destroy(reinterpret_cast<glm_batch>(B));
+    return set_error(GLM_ENOMEM, "batch flag words: device allocation failed");
   }
   B->pr.resize(P);
   for (int p = 0; p < P; ++p) {
@@ -509,7 +524,16 @@ int glm_batch_run(glm_batch bt, float *const *xs, int *status) {
   }
   GLM_CUDA_TRY(cudaGraphLaunch(B->graph, B->stream));
   GLM_CUDA_TRY(cudaStreamSynchronize(B->stream));
+  unsigned gflag = 0;
+  GLM_CUDA_TRY(cudaMemcpy(&gflag, B->bflag, sizeof(unsigned), cudaMemcpyDeviceToHost));
   int worst = GLM_OK;
+  if (gflag) {  // a Gram launch gave up a bounded wait: every problem's G is suspect
+    GLM_CUDA_TRY(cudaMemset(B->bflag, 0, sizeof(unsigned)));
+    for (int p = 0; p < B->P; ++p) glm_sync(B->pr[p].h);  // clear the problems' flags
+    if (status)
+      for (int p = 0; p < B->P; ++p) status[p] = GLM_ETIMEOUT;
+    return set_error(GLM_ETIMEOUT, "a Gram launch of the batch gave up a bounded device wait");
+  }
   for (int p = 0; p < B->P; ++p) {
     const int rc = glm_sync(B->pr[p].h);  // reads and clears the problem's flag
     if (status) status[p] = rc;

@@ -29,6 +29,10 @@ int cuda_error(cudaError_t e, const char *what);
     if (e_ != cudaSuccess) return ::glm::cuda_error(e_, #expr);                \
   } while (0)
 
+// Device allocation through the failure-injection hook (glm_debug_fail_alloc);
+// returns the CUDA status (cudaErrorMemoryAllocation when injected).
+cudaError_t dev_malloc(void **p, size_t bytes);
+
 #define GLM_TRY(expr)                                                          \
   do {                                                                         \
     int rc_ = (expr);                                                          \
@@ -372,7 +376,7 @@ struct DevBuf {
 struct RunKey {
   int s = 0, gram_dt = 0, gemv_dt = 0, rec64 = 0, kahan = 0, cluster = 0,
       gram_impl = 0, sgd = 0, timing = 0;
-  int64_t b = 0, iters = 0, first_iter = 0, chunk = 0;
+  int64_t b = 0, iters = 0, first_iter = 0, chunk = 0, probe = 0;
   uint64_t seed = 0;
   uint32_t problem = 0;
   float eta = 0.f, lambda = 0.f;
@@ -432,6 +436,7 @@ struct GramArgs {
   int s; int64_t b, n;
   float *G;
   unsigned *flag;         // device flag word for FLAG_TIMEOUT, or null
+  long long probe;        // > 0: failure-path probe wait (SM cycles), else 0
 };
 int launch_gram_simt(const GramArgs &a, cudaStream_t st);
 int launch_gram_tc(const GramArgs &a, cudaStream_t st);
@@ -453,6 +458,7 @@ struct ChainArgs {
   int rec64, kahan, cluster;
   int64_t sbp;            // labels of outer step h start at ylab[h * sbp]
   int prefetch;           // 1: stage Y / labels / G through shared memory
+  long long probe;        // > 0: failure-path probe wait (SM cycles), else 0
   double cpow[257];    // c^j, j = 0..s
   double cinv[257];    // c^-j
 };

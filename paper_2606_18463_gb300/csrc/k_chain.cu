@@ -461,6 +461,24 @@ k_chain(const __grid_constant__ ChainArgs a) {
     issue_gs(1);
     for (int kb = 0; kb < ngs; ++kb) issue_gb(kb);
   }
+  bool abort = false;
+  if (a.probe > 0) {
+    // failure-path probe: thread 0 waits on a barrier that nothing signals
+    // (pipeline barrier 1 is otherwise unused) and gives up.  The cluster
+    // agrees on the outcome before any data moves between CTAs, so an abort
+    // here leaves no exchange store in flight.
+    if (tid == 0 && !mbar_wait_bounded(bar0 + 8, 0, a.probe)) atomicOr(&s_abort, 1);
+    cluster.sync();
+    int any = 0;
+    if (tid < C) {
+      uint32_t v;
+      asm volatile("ld.shared::cluster.u32 %0, [%1];"
+                   : "=r"(v) : "r"(mapa(smem_u32(&s_abort), (uint32_t)tid)) : "memory");
+      any = v != 0;
+    }
+    abort = __syncthreads_or(any) != 0;
+    cluster.sync();  // every CTA has read every other's flag before any can change
+  }
 
   // ========================= consumer warps ==================================
   const int V = kV ? kV : nc / 8;    // 8-element vectors in the slice
@@ -479,7 +497,6 @@ k_chain(const __grid_constant__ ChainArgs a) {
   const TY *Y = static_cast<const TY *>(a.Y);
   int gslot = 0;          // G_BLOCK: slot of the next block row (kept as a counter:
   uint32_t gpar = 0;      //   no division on the recurrence's path) and its phase parity
-  bool abort = false;
   // update: 0 = folded in block by block by the workers, 1 = after the
   // recurrence by every consumer thread (row groups), 2 = after the
   // recurrence, one thread per 8-column vector (slices wider than that)
@@ -974,6 +991,16 @@ k_chain(const __grid_constant__ ChainArgs a) {
       if (col0 + c < n) a.x[col0 + c] = xs[c];
   }
   cluster.sync();
+  if (abort && tid == 0) {
+    // A CTA that gave up mid-step may have exchange stores (st.async) in
+    // flight towards it that no barrier wait will observe.  Every CTA has
+    // stopped issuing them (they all passed the barrier above); wait about
+    // 20 us, far beyond the DSMEM one-way latency (under 1 us), before this
+    // CTA's shared memory is released.
+    const long long t0 = clock64();
+    while (clock64() - t0 < 40000) {
+    }
+  }
 }
 
 cudaLaunchConfig_t make_cfg(int C, size_t smem, cudaStream_t st, cudaLaunchAttribute *attr) {

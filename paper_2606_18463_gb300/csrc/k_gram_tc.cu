@@ -46,6 +46,7 @@ struct TcArgs {
   const float *rs;        // per-row scales (E4M3) or null
   float *G;
   unsigned *flag;
+  long long probe;        // > 0: failure-path probe wait before the first MMA
   int64_t nouter, rows, b, n, ld;
   int s, dt, nk;          // nk: K chunks
 };
@@ -108,6 +109,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Bounded wait that also gives up once another role of the CTA has aborted
+// (the abort flag is read on every 64th probe).
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
+                                              const volatile int *abort_flag) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (unsigned k = 1;; ++k) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((k & 63) == 0 && (*abort_flag || clock64() - t0 > kBudget)) return false;
+  }
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
@@ -183,6 +196,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
   const uint32_t full0 = bars, empty0 = bars + 8 * kStages;
   const uint32_t tfull0 = bars + 16 * kStages, tempty0 = tfull0 + 16;
   const uint32_t drain = tempty0 + 16;        // MMA unwind barrier
+  const uint32_t probe_bar = drain + 8;       // never signalled (failure-path probe)
   const uint32_t tmem_slot = drain + 16;      // 16-byte aligned TMEM address slot
   __shared__ int s_abort;
 
@@ -197,6 +211,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
       mbar_init(tempty0 + 8 * i, 4);  // one arrival per epilogue warp
     }
     mbar_init(drain, 1);
+    mbar_init(probe_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
@@ -226,7 +241,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
         for (int kc = 0; kc < a.nk; ++kc, ++it) {
           const int st = (int)(it % kStages);
           if (it >= kStages &&
-              !mbar_wait_bounded(empty0 + 8 * st, (uint32_t)((it / kStages - 1) & 1), kBudget)) {
+              !wait_or_abort(empty0 + 8 * st, (uint32_t)((it / kStages - 1) & 1), vabort)) {
             atomicOr(&s_abort, 1);
             break;
           }
@@ -251,12 +266,14 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
     if (lane == 0) {
       constexpr uint32_t idesc = instr_desc<DT, kN>();
       int64_t it = 0, tc = 0;
+      // failure-path probe: a wait on a barrier nothing signals gives up
+      if (a.probe > 0 && !mbar_wait_bounded(probe_bar, 0, a.probe)) atomicOr(&s_abort, 1);
       for (int64_t t = blockIdx.x; t < ntiles && !*vabort; t += gridDim.x) {
         Tile tl;
         if (!tile_at<kN>(a, P, t, tl)) continue;
         const int buf = (int)(tc & 1);
         if (tc >= 2 &&
-            !mbar_wait_bounded(tempty0 + 8 * buf, (uint32_t)((tc / 2 - 1) & 1), kBudget)) {
+            !wait_or_abort(tempty0 + 8 * buf, (uint32_t)((tc / 2 - 1) & 1), vabort)) {
           atomicOr(&s_abort, 1);
           break;
         }
@@ -265,7 +282,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
         bool ok = true;
         for (int kc = 0; kc < a.nk; ++kc, ++it) {
           const int st = (int)(it % kStages);
-          if (!mbar_wait_bounded(full0 + 8 * st, (uint32_t)((it / kStages) & 1), kBudget)) {
+          if (!wait_or_abort(full0 + 8 * st, (uint32_t)((it / kStages) & 1), vabort)) {
             atomicOr(&s_abort, 1);
             ok = false;
             break;
@@ -296,7 +313,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
       Tile tl;
       if (!tile_at<kN>(a, P, t, tl)) continue;
       const int buf = (int)(tc & 1);
-      if (!mbar_wait_bounded(tfull0 + 8 * buf, (uint32_t)((tc / 2) & 1), kBudget)) {
+      if (!wait_or_abort(tfull0 + 8 * buf, (uint32_t)((tc / 2) & 1), vabort)) {
         atomicOr(&s_abort, 1);
         break;
       }
@@ -382,6 +399,7 @@ int launch_gram_tc(const GramArgs &g, cudaStream_t st) {
   a.rs = g.rs;
   a.G = g.G;
   a.flag = g.flag;
+  a.probe = g.probe;
   a.nouter = g.nouter;
   a.rows = g.rows;
   a.b = g.b;

@@ -37,7 +37,7 @@ EXPORTED = [
     "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_sgd_lowp_run", "glm_ca_sgd_run",
     "glm_ca_sgd_run_ex", "glm_ca_plan", "glm_kernel_times", "glm_loss",
     "glm_sample_indices", "glm_sample_indices_noalloc", "glm_gram_lower",
-    "glm_storage_layout", "glm_storage_read",
+    "glm_storage_layout", "glm_storage_read", "glm_debug_fail_alloc",
     "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
     "glm_batch_choice", "glm_batch_destroy",
 ]
@@ -61,7 +61,7 @@ class glm_ca_opts(ctypes.Structure):
                 ("first_iter", ctypes.c_int64), ("problem", ctypes.c_uint32),
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("chunk_outer", ctypes.c_int64), ("gram_impl", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("wait_probe_cycles", ctypes.c_int64)]
 
 
 class glm_run_plan(ctypes.Structure):
@@ -81,7 +81,8 @@ class glm_problem_desc(ctypes.Structure):
 
 class glm_batch_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("input_dtype", ctypes.c_int),
-                ("input_on_host", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("input_on_host", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("wait_probe_cycles", ctypes.c_int64)]
 
 
 _lib = None
@@ -130,6 +131,7 @@ def load():
             "glm_storage_layout": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)], i32),
             "glm_storage_read": ([vp, i64, i64, vp, vp, vp, vp], i32),
+            "glm_debug_fail_alloc": ([i64], None),
             "glm_batch_opts_default": ([ctypes.POINTER(glm_batch_opts)], None),
             "glm_batch_create": ([i32, ctypes.POINTER(glm_problem_desc),
                                   ctypes.POINTER(glm_batch_opts), ctypes.POINTER(vp)], i32),
@@ -278,6 +280,12 @@ def glm_storage_read(h, row0, rows, A_out=None, colscale_out=None, fp8_out=None,
                                    _ptr(fp8_out), _ptr(rowscale_out)))
 
 
+def glm_debug_fail_alloc(after: int) -> None:
+    """Failure-path test hook: the allocation after the next `after` ones
+    fails with GLM_ENOMEM; a negative value disarms it."""
+    load().glm_debug_fail_alloc(after)
+
+
 def glm_stream(h) -> int:
     return load().glm_stream(h)
 
@@ -408,7 +416,7 @@ class Batch:
     A (host numpy (m, n) float32), y, loss, lam, eta, iters, seed, b and
     optionally s (0 = autotuned) and gram ('f32', 'tf32', 'bf16', 'f16')."""
 
-    def __init__(self, problems, dtype="bf16", stream=None):
+    def __init__(self, problems, dtype="bf16", stream=None, wait_probe_cycles=0):
         import numpy as np
         import torch
         self._keep = []
@@ -432,6 +440,7 @@ class Batch:
         o.input_on_host = 1
         st = stream if stream is not None else torch.cuda.current_stream()
         o.stream = st.cuda_stream or 1
+        o.wait_probe_cycles = wait_probe_cycles
         self.stream = st
         self.P = len(descs)
         self.h = glm_batch_create(self.P, descs, o)
