@@ -328,6 +328,47 @@ int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b,
                    int64_t n, int64_t ld, const float *row_scale, float *G,
                    int impl, void *stream);
 
+/* ---- column-partitioned CA-SGD (P ranks) ---------------------------------- */
+/*
+ * Paper Algorithm 1 on P ranks with the 1D block-column partition (Sec. 4):
+ * rank p holds a column slab A_p of A (its own handle, created from those
+ * columns with every row and the same labels) and the matching slab x_p of
+ * the iterate.  Every rank draws the same rows (same seed and stream id).
+ * One outer iteration of sh inner steps (1 <= sh <= s; sh < s only for a
+ * run's last, shorter block) is:
+ *   glm_slab_partial(rank p)   red_p = [ r_p | G_p ]
+ *   red = sum over p of red_p  (the grouped AllReduce of Sec. 6, done by the
+ *                               caller: NCCL/gloo across processes, or
+ *                               glm_sum_buffers across ranks emulated on one
+ *                               device)
+ *   glm_slab_finish(rank p)    recurrence on red, update of x_p
+ * red holds glm_slab_reduce_floats(s, b) floats: the partial margins
+ * r_p = Y_p x_p in red[0 .. round_up(s b, 4)) (zeros past sh b), then the
+ * strictly block-lower Gram of the step's rows over the slab's columns in the
+ * packed row-block layout of glm_gram_lower (zeros for blocks >= sh).  The
+ * recurrence is the same on every rank, so the slabs stay one iterate; in
+ * exact arithmetic P ranks equal one rank (and SGD).  Precision options are
+ * those of glm_ca_opts (gram_dtype, gemv_dtype, recurrence_f64, kahan,
+ * gram_impl, problem; first_iter and the graph/cluster/chunk/timing options
+ * are ignored).  s b <= 8192.  Both calls enqueue on the handle's stream; a
+ * finish must follow its partial on the same handle with the same s, b, sh.
+ */
+int glm_slab_reduce_floats(int s, int64_t b, int64_t *count);
+/* Gather the step's rows (SGD-equivalent iterations first_iter .. first_iter
+ * + sh - 1, draws first_iter b ..), write red.  x: device FP32[n_p] (read);
+ * red: device FP32[glm_slab_reduce_floats] (written). */
+int glm_slab_partial(glm_handle h, int s, int64_t b, int sh, uint64_t seed, int64_t first_iter,
+                     const float *x, float *red, const glm_ca_opts *opts);
+/* Run the recurrence on the summed red (read) and update x (device FP32[n_p],
+ * in/out): x <- c^sh x - alpha sum_j c^{sh-1-j} Y_{j,p}^T u_j. */
+int glm_slab_finish(glm_handle h, int s, int64_t b, int sh, float eta, float lambda,
+                    const float *red, float *x, const glm_ca_opts *opts);
+/* dst[i] = srcs[0][i] + srcs[1][i] + ... + srcs[P-1][i] in rank order, FP32
+ * (the reduction of ranks emulated on one device).  srcs: host array of P
+ * device pointers, 1 <= P <= 64; dst may be one of them.  stream: cudaStream_t
+ * or NULL (legacy default stream).  Enqueues and returns. */
+int glm_sum_buffers(float *dst, const float *const *srcs, int P, int64_t count, void *stream);
+
 /* ---- batched fits -------------------------------------------------------- */
 /*
  * No counterpart in the paper (its experiments fit one problem at a time):

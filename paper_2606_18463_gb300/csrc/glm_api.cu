@@ -452,6 +452,26 @@ int run_common(Handle *h, int s, int64_t b, float eta, float lambda, int64_t ite
 }
 
 }  // namespace
+
+// The precision slots, Gram kernel and stream id a run with these arguments
+// resolves to (the column-partitioned steps use the fused path's rules).
+int resolve_public(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
+                   uint64_t seed, float *x, const glm_ca_opts *o, int &gram_dt, int &gemv_dt,
+                   int &rec64, int &kahan, int &gram_impl, int64_t &ld_gram, int64_t &ld_gemv,
+                   uint32_t &problem) {
+  RunPlan p;
+  GLM_TRY(resolve(h, s, b, eta, lambda, iters, seed, x, o, false, p));
+  gram_dt = p.gram_dt;
+  gemv_dt = p.gemv_dt;
+  rec64 = p.rec64;
+  kahan = p.kahan;
+  gram_impl = p.gram_impl;
+  ld_gram = p.ld_gram;
+  ld_gemv = p.ld_gemv;
+  problem = p.problem;
+  return GLM_OK;
+}
+
 }  // namespace glm
 
 using namespace glm;

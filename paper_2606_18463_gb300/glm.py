@@ -38,6 +38,7 @@ EXPORTED = [
     "glm_ca_sgd_run_ex", "glm_ca_plan", "glm_kernel_times", "glm_loss",
     "glm_sample_indices", "glm_sample_indices_noalloc", "glm_gram_lower",
     "glm_storage_layout", "glm_storage_read", "glm_debug_fail_alloc",
+    "glm_slab_reduce_floats", "glm_slab_partial", "glm_slab_finish", "glm_sum_buffers",
     "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
     "glm_batch_choice", "glm_batch_destroy",
 ]
@@ -132,6 +133,12 @@ def load():
                                     ctypes.POINTER(i64)], i32),
             "glm_storage_read": ([vp, i64, i64, vp, vp, vp, vp], i32),
             "glm_debug_fail_alloc": ([i64], None),
+            "glm_slab_reduce_floats": ([i32, i64, ctypes.POINTER(i64)], i32),
+            "glm_slab_partial": ([vp, i32, i64, i32, u64, i64, vp, vp,
+                                  ctypes.POINTER(glm_ca_opts)], i32),
+            "glm_slab_finish": ([vp, i32, i64, i32, f32, f32, vp, vp,
+                                 ctypes.POINTER(glm_ca_opts)], i32),
+            "glm_sum_buffers": ([vp, ctypes.POINTER(vp), i32, i64, vp], i32),
             "glm_batch_opts_default": ([ctypes.POINTER(glm_batch_opts)], None),
             "glm_batch_create": ([i32, ctypes.POINTER(glm_problem_desc),
                                   ctypes.POINTER(glm_batch_opts), ctypes.POINTER(vp)], i32),
@@ -284,6 +291,27 @@ def glm_debug_fail_alloc(after: int) -> None:
     """Failure-path test hook: the allocation after the next `after` ones
     fails with GLM_ENOMEM; a negative value disarms it."""
     load().glm_debug_fail_alloc(after)
+
+
+def glm_slab_reduce_floats(s, b) -> int:
+    c = ctypes.c_int64()
+    _check(load().glm_slab_reduce_floats(s, b, ctypes.byref(c)))
+    return c.value
+
+
+def glm_slab_partial(h, s, b, sh, seed, first_iter, x, red, opts=None) -> None:
+    _check(load().glm_slab_partial(h, s, b, sh, seed, first_iter, _ptr(x), _ptr(red),
+                                   ctypes.byref(opts) if opts is not None else None))
+
+
+def glm_slab_finish(h, s, b, sh, eta, lam, red, x, opts=None) -> None:
+    _check(load().glm_slab_finish(h, s, b, sh, eta, lam, _ptr(red), _ptr(x),
+                                  ctypes.byref(opts) if opts is not None else None))
+
+
+def glm_sum_buffers(dst, srcs, count, stream=None) -> None:
+    arr = (ctypes.c_void_p * len(srcs))(*[_ptr(t) for t in srcs])
+    _check(load().glm_sum_buffers(_ptr(dst), arr, len(srcs), count, stream))
 
 
 def glm_stream(h) -> int:
