@@ -121,11 +121,17 @@ typedef struct {
   int gemv_dtype;     /* u_r = u_g (margin and outer-gradient operands);
                          -1 (default) = gram_dtype, or the storage type when
                          gram_dtype is GLM_E4M3.                              */
-  int recurrence_f64; /* u_c: -1 (default) FP64 iff s >= 32, 0 FP32, 1 FP64.
-                         In FP64 the correction sums and residual history
-                         are FP64 and each residual (u_sigma) is the FP32
-                         loss derivative of the FP64 margin; in FP32 the
-                         residual uses the fast exponential and division.  */
+  int recurrence_f64; /* u_c: -1 (default) FP64 iff s >= 32, 0 FP32, 1 FP64,
+                         2 compensated FP32.  In FP64 the correction sums and
+                         residual history are FP64 and each residual
+                         (u_sigma) is the FP32 loss derivative of the FP64
+                         margin; in FP32 the residual uses the fast
+                         exponential and division.  Compensated FP32 (the
+                         streaming chain only): FP32 products with per-lane
+                         Kahan sums combined in FP64, residual as in FP64
+                         mode -- the correction's error stays near
+                         2 u_32 sum |G| |u| whatever its length, like FP64
+                         sums, at FP32 rates (GB300's FP64 rate is 1/64).     */
   int kahan;          /* 1 (default): Kahan-compensated FP32 Y^T u sums.      */
   int64_t first_iter; /* SGD-equivalent iteration the run starts at; draws
                          continue the counter-based stream from there, so a
@@ -139,11 +145,19 @@ typedef struct {
   int64_t chunk_outer;/* outer iterations staged per chunk; 0 = automatic.   */
   int gram_impl;      /* 0 (default) automatic, 1 SIMT FP32 kernel,
                          2 tcgen05 tensor-core kernel, 3 SIMT kernel with
-                         FP16 accumulation (Recipe F's Gram slot: FP16
+                         FP16 accumulation, 4 tcgen05 kernel with an FP16
+                         accumulator (3 and 4: Recipe F's Gram slot, FP16
                          input and accumulation; gram_dtype GLM_F16 only,
                          else GLM_EINVAL; never chosen automatically).       */
   int timing;         /* 1: record CUDA events around every kernel of the run
                          (read back with glm_kernel_times).  Default 0.       */
+  int chain_impl;     /* x-dependent chain kernel: 0 (default) automatic, 1
+                         resident (the step's Y and G staged whole in the
+                         cluster's shared memory), 2 streaming (Y and G
+                         streamed through shared-memory rings: wide rows,
+                         long blocks).  Automatic takes the streaming kernel
+                         when the resident one cannot stage the step, or for
+                         recurrence_f64 = 2.                                  */
   int64_t wait_probe_cycles;
                       /* Failure-path test hook; 0 (default) = off.  When > 0,
                          one thread of every CTA of the chain and tcgen05
@@ -165,6 +179,7 @@ typedef struct {
   int cluster;          /* CTAs in the chain cluster                          */
   int gram_impl;        /* 1 SIMT, 2 tcgen05, 3 SIMT FP16 accumulation       */
   int gram_dtype, gemv_dtype, recurrence_f64;
+  int chain_impl;       /* 1 resident, 2 streaming                            */
 } glm_run_plan;
 
 int glm_ca_plan(glm_handle h, int s, int64_t b, float eta, float lambda,
@@ -320,8 +335,9 @@ int glm_storage_read(glm_handle h, int64_t row0, int64_t rows, void *A_out,
  * G[j b + l][0 .. j b) at float offset g Z + b (ld_1 + ... + ld_{j-1}) +
  * l ld_j, where Z = b (ld_1 + ... + ld_{s-1}) floats per group; the padding
  * floats of a row hold no result.  impl: 0 auto, 1 SIMT FP32, 2 tcgen05, 3
- * SIMT with FP16 accumulation (GLM_F16 only, else GLM_EINVAL).  ld must be a
- * multiple of 64 for impl 2.  stream: cudaStream_t or NULL (legacy default
+ * SIMT with FP16 accumulation, 4 tcgen05 with an FP16 accumulator (3 and 4:
+ * GLM_F16 only, else GLM_EINVAL).  ld must be a multiple of 64 for impl 2
+ * and 4.  stream: cudaStream_t or NULL (legacy default
  * stream).
  */
 int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b,

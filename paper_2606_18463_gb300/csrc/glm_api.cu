@@ -70,7 +70,8 @@ bool RunKey::operator==(const RunKey &o) const {
          kahan == o.kahan && cluster == o.cluster && gram_impl == o.gram_impl &&
          sgd == o.sgd && b == o.b && iters == o.iters && first_iter == o.first_iter &&
          chunk == o.chunk && seed == o.seed && problem == o.problem && eta == o.eta &&
-         lambda == o.lambda && x == o.x && timing == o.timing && probe == o.probe;
+         lambda == o.lambda && x == o.x && timing == o.timing && probe == o.probe &&
+         chain == o.chain;
 }
 
 int loss_partials_needed();
@@ -119,7 +120,7 @@ struct RunPlan {
   int s = 1;
   int64_t b = 1, iters = 0, H = 0, chunk = 1;
   int gram_dt = GLM_F32, gemv_dt = GLM_F32, rec64 = 0, kahan = 1, cluster = 1;
-  int gram_impl = 1, sgd = 0, use_graph = 1, timing = 0;
+  int gram_impl = 1, sgd = 0, use_graph = 1, timing = 0, chain_impl = 1;
   int64_t chunks = 0, launches = 0;
   int64_t ld_gram = 0, ld_gemv = 0;  // 0 ld_gemv: GEMV reads the Gram copy
   float eta = 0.f, lambda = 0.f, alpha = 0.f;
@@ -178,16 +179,22 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
     return set_error(GLM_EINVAL, "gemv_dtype must be F32, TF32, BF16 or F16");
   p.gram_dt = gdt;
   p.gemv_dt = vdt;
-  p.rec64 = o->recurrence_f64 < 0 ? (s >= 32 ? 1 : 0) : (o->recurrence_f64 ? 1 : 0);
+  if (o->recurrence_f64 < -1 || o->recurrence_f64 > 2)
+    return set_error(GLM_EINVAL, "recurrence_f64 must be -1, 0, 1 or 2");
+  p.rec64 = o->recurrence_f64 < 0 ? (s >= 32 ? 1 : 0) : o->recurrence_f64;
+  if (o->chain_impl < 0 || o->chain_impl > 2)
+    return set_error(GLM_EINVAL, "chain_impl must be 0, 1 or 2");
   p.ld_gram = round_up(h->n, gdt == GLM_E4M3 ? 128 : 64);
   p.ld_gemv = (vdt == gdt) ? 0 : round_up(h->n, 64);
   // Gram implementation
   if (o->gram_impl == 2 && !gram_tc_supported(gdt, p.ld_gram))
     return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram does not support this operand type");
-  if (o->gram_impl == 3 && gdt != GLM_F16)
-    return set_error(GLM_EINVAL, "gram_impl 3 (FP16 accumulation) needs gram_dtype GLM_F16");
+  if ((o->gram_impl == 3 || o->gram_impl == 4) && gdt != GLM_F16)
+    return set_error(GLM_EINVAL, "gram_impl 3/4 (FP16 accumulation) needs gram_dtype GLM_F16");
+  if (o->gram_impl == 4 && !gram_tc_supported(gdt, round_up(h->n, 64)))
+    return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram does not support this operand type");
   p.gram_impl = o->gram_impl == 0 ? (gram_tc_supported(gdt, p.ld_gram) ? 2 : 1) : o->gram_impl;
-  if (p.gram_impl < 1 || p.gram_impl > 3) return set_error(GLM_EINVAL, "gram_impl");
+  if (p.gram_impl < 1 || p.gram_impl > 4) return set_error(GLM_EINVAL, "gram_impl");
   // chunking
   p.H = (iters + s - 1) / s;
   const int64_t sb = (int64_t)s * b;
@@ -209,11 +216,13 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
   probe.n = h->n;
   probe.b = b;
   probe.s = s;
-  probe.rec64 = p.rec64;
+  probe.rec64 = p.rec64 == 1 ? 1 : 0;
   probe.prefetch = 1;
-  const int cmax = chain_max_cluster(probe);
+  const int cmax_res = chain_max_cluster(probe);
+  const int cmax = std::max(cmax_res, 16);  // the streaming chain fits any cluster width
   if (cmax < 1)
     return set_error(GLM_EUNSUPPORTED, "s*b too large for the on-chip recurrence state");
+  (void)cmax;
   int C = o->cluster;
   if (C <= 0) {
     // widest cluster that keeps >= 4 rows of each block and >= 32 columns
@@ -227,6 +236,25 @@ int resolve(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
     return set_error(GLM_EINVAL, "cluster must be a power of two in [1, 16]");
   while (C > 1 && !chain_cluster_ok(C, b)) C /= 2;
   p.cluster = C;
+  // chain kernel: resident when it stages the step (and the recurrence is
+  // FP32 / FP64), else streaming
+  probe.cluster = C;
+  probe.ldy = p.ld_gemv ? p.ld_gemv : p.ld_gram;
+  const bool res_ok = cmax_res >= C && p.rec64 != 2 && chain_resident_staged(probe);
+  probe.rec64 = p.rec64;
+  const bool str_ok = chain_stream_ok(probe);
+  if (o->chain_impl == 1) {
+    if (p.rec64 == 2) return set_error(GLM_EINVAL, "the resident chain has no compensated FP32 mode");
+    if (cmax_res < C) return set_error(GLM_EUNSUPPORTED, "s*b too large for the resident chain");
+    p.chain_impl = 1;
+  } else if (o->chain_impl == 2) {
+    if (!str_ok) return set_error(GLM_EUNSUPPORTED, "shape outside the streaming chain's limits");
+    p.chain_impl = 2;
+  } else {
+    p.chain_impl = res_ok || (!str_ok && p.rec64 != 2 && cmax_res >= C) ? 1 : 2;
+    if (p.chain_impl == 2 && !str_ok)
+      return set_error(GLM_EUNSUPPORTED, "s*b too large for the on-chip recurrence state");
+  }
   p.chunks = (p.H + p.chunk - 1) / p.chunk;
   p.launches = p.chunks * (s > 1 ? 3 : 2);
   return GLM_OK;
@@ -383,6 +411,7 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
       GLM_TRY(tmark(h, p, side, ci, 1, 0));
       if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, side));
       else if (p.gram_impl == 3) GLM_TRY(launch_gram_simt_f16acc(gr, side));
+      else if (p.gram_impl == 4) GLM_TRY(launch_gram_tc_f16acc(gr, side));
       else GLM_TRY(launch_gram_simt(gr, side));
       GLM_TRY(tmark(h, p, side, ci, 1, 1));
     }
@@ -391,7 +420,8 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
     ca.nouter = (int)nout;
     ca.s_last = s_last;
     GLM_TRY(tmark(h, p, st, ci, 2, 0));
-    GLM_TRY(launch_chain(ca, st));
+    if (p.chain_impl == 2) GLM_TRY(launch_chain_stream(ca, st));
+    else GLM_TRY(launch_chain(ca, st));
     GLM_TRY(tmark(h, p, st, ci, 2, 1));
     GLM_CUDA_TRY(cudaEventRecord(h->ev_chain[buf], st));
   }
@@ -413,7 +443,7 @@ int run_common(Handle *h, int s, int64_t b, float eta, float lambda, int64_t ite
   key.kahan = p.kahan; key.cluster = p.cluster; key.gram_impl = p.gram_impl; key.sgd = p.sgd;
   key.b = p.b; key.iters = p.iters; key.first_iter = p.first_iter; key.chunk = p.chunk;
   key.seed = p.seed; key.problem = p.problem; key.eta = p.eta; key.lambda = p.lambda;
-  key.x = p.x; key.timing = p.timing; key.probe = p.probe;
+  key.x = p.x; key.timing = p.timing; key.probe = p.probe; key.chain = p.chain_impl;
   if (realloc && h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -504,6 +534,7 @@ void glm_ca_opts_default(glm_ca_opts *o) {
   o->chunk_outer = 0;
   o->gram_impl = 0;
   o->timing = 0;
+  o->chain_impl = 0;
   o->wait_probe_cycles = 0;
 }
 
@@ -753,6 +784,7 @@ int glm_ca_plan(glm_handle hh, int s, int64_t b, float eta, float lambda, int64_
   out->gram_dtype = p.gram_dt;
   out->gemv_dtype = p.gemv_dt;
   out->recurrence_f64 = p.rec64;
+  out->chain_impl = p.chain_impl;
   return GLM_OK;
 }
 
@@ -890,7 +922,13 @@ int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b, i
     if (dtype != GLM_F16) return set_error(GLM_EINVAL, "impl 3 (FP16 accumulation) needs GLM_F16");
     return launch_gram_simt_f16acc(a, st);
   }
-  if (impl != 1) return set_error(GLM_EINVAL, "impl must be 0, 1, 2 or 3");
+  if (impl == 4) {
+    if (dtype != GLM_F16) return set_error(GLM_EINVAL, "impl 4 (FP16 accumulation) needs GLM_F16");
+    if (!gram_tc_supported(dtype, ld))
+      return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram: ld % 64 != 0");
+    return launch_gram_tc_f16acc(a, st);
+  }
+  if (impl != 1) return set_error(GLM_EINVAL, "impl must be 0, 1, 2, 3 or 4");
   return launch_gram_simt(a, st);
 }
 

@@ -377,6 +377,7 @@ struct RunKey {
   int s = 0, gram_dt = 0, gemv_dt = 0, rec64 = 0, kahan = 0, cluster = 0,
       gram_impl = 0, sgd = 0, timing = 0;
   int64_t b = 0, iters = 0, first_iter = 0, chunk = 0, probe = 0;
+  int chain = 0;
   uint64_t seed = 0;
   uint32_t problem = 0;
   float eta = 0.f, lambda = 0.f;
@@ -440,6 +441,8 @@ struct GramArgs {
 };
 int launch_gram_simt(const GramArgs &a, cudaStream_t st);
 int launch_gram_tc(const GramArgs &a, cudaStream_t st);
+// tcgen05 Gram of F16 operands with an F16 accumulator (Recipe F's Gram slot)
+int launch_gram_tc_f16acc(const GramArgs &a, cudaStream_t st);
 bool gram_tc_supported(int dt, int64_t ld);
 
 // residual-path division: reciprocal rounded to nearest (one extra rounding)
@@ -463,6 +466,11 @@ struct ChainArgs {
   double cinv[257];    // c^-j
 };
 int launch_chain(const ChainArgs &a, cudaStream_t st);
+// 1 when the resident chain (k_chain) stages this shape's Y and G on chip
+bool chain_resident_staged(const ChainArgs &a);
+// streaming chain (k_chain_stream): layout limits and launch
+bool chain_stream_ok(const ChainArgs &a);
+int launch_chain_stream(const ChainArgs &a, cudaStream_t st);
 int chain_max_cluster(const ChainArgs &a);
 bool chain_cluster_ok(int C, int64_t b);
 

@@ -302,6 +302,7 @@ int glm_slab_partial(glm_handle hh, int s, int64_t b, int sh, uint64_t seed, int
     gr.flag = h->dflag;
     if (st.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, cs));
     else if (st.gram_impl == 3) GLM_TRY(launch_gram_simt_f16acc(gr, cs));
+    else if (st.gram_impl == 4) GLM_TRY(launch_gram_tc_f16acc(gr, cs));
     else GLM_TRY(launch_gram_simt(gr, cs));
   }
   return GLM_OK;

@@ -1092,6 +1092,12 @@ int max_cluster_t(const ChainArgs &a) {
 
 bool chain_cluster_ok(int C, int64_t b) { return cluster_rows_ok(C, b); }
 
+bool chain_resident_staged(const ChainArgs &a) {
+  const int tr = a.rec64 ? 8 : 4;
+  const Layout L = make_layout(a.n, a.b, a.s, a.cluster, tr, elem_bytes(a.dt), 1);
+  return L.total <= kSmemMax && L.ns > 0 && (a.s < 2 || L.gmode != G_NONE);
+}
+
 int chain_max_cluster(const ChainArgs &a) {
   const bool f64 = a.rec64 != 0;
   switch (a.dt) {

@@ -19,7 +19,9 @@
 //               (E4M3), masked FP32 stores into the padded row-block layout.
 // Operand kinds: BF16 / F16 (kind::f16), TF32 (kind::tf32, FP32 container
 // already rounded to TF32), E4M3 (kind::f8f6f4, one power-of-two scale per row
-// applied at readout).  Accumulation is FP32 throughout.  Every mbarrier wait
+// applied at readout).  Accumulation is FP32, except for the FP16-accumulate
+// instance (Recipe F's Gram slot: F16 operands, F16 accumulator in TMEM --
+// one value in the low half of each 32-bit column -- widened at readout).  Every mbarrier wait
 // is bounded; on timeout the kernel records FLAG_TIMEOUT, drains its own
 // work (bounded) and frees its TMEM.
 #include "glm_internal.cuh"
@@ -135,11 +137,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: D FP32, A/B K-major, M = 128, N = kN.
-template <int DT, int kN> __host__ __device__ constexpr uint32_t instr_desc() {
+// Instruction descriptor: D FP32 (or F16), A/B K-major, M = 128, N = kN.
+template <int DT, int kN, bool kAcc16 = false>
+__host__ __device__ constexpr uint32_t instr_desc() {
   // operand format field: kind::f16 -> F16 0 / BF16 1; kind::tf32 -> 2;
-  // kind::f8f6f4 -> E4M3 0
-  return (1u << 4)                                                      // D = F32
+  // kind::f8f6f4 -> E4M3 0; accumulator format: F16 0, F32 1
+  return ((kAcc16 ? 0u : 1u) << 4)                                     // D format
          | ((uint32_t)(DT == GLM_BF16 ? 1 : DT == GLM_TF32 ? 2 : 0) << 7)  // A format
          | ((uint32_t)(DT == GLM_BF16 ? 1 : DT == GLM_TF32 ? 2 : 0) << 10) // B format
          | ((uint32_t)(kN >> 3) << 17)                                  // N >> 3
@@ -183,7 +186,7 @@ __device__ __forceinline__ bool tile_at(const TcArgs &a, int64_t P, int64_t t, T
   return r_last >= r0 && r_last / a.b > c0 / a.b;
 }
 
-template <int DT, int kN>
+template <int DT, int kN, bool kAcc16 = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const __grid_constant__ TcArgs a) {
   using Cfg = TileCfg<kN>;
@@ -264,7 +267,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      constexpr uint32_t idesc = instr_desc<DT, kN>();
+      constexpr uint32_t idesc = instr_desc<DT, kN, kAcc16>();
       int64_t it = 0, tc = 0;
       // failure-path probe: a wait on a barrier nothing signals gives up
       if (a.probe > 0 && !mbar_wait_bounded(probe_bar, 0, a.probe)) atomicOr(&s_abort, 1);
@@ -329,6 +332,11 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
         float v[32];
         tmem_ld32(tmem_base + (uint32_t)(buf * kN + cc * 32) + ((uint32_t)(quad * 32) << 16),
                   v);
+        if (kAcc16) {  // F16 accumulator: the low 16 bits of each column
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            v[i] = __half2float(__ushort_as_half((unsigned short)(__float_as_uint(v[i]) & 0xFFFFu)));
+        }
         const int64_t c0 = tl.ti * kN + cc * 32;
         if (!row_ok || c0 >= limit) continue;
         if (DT == GLM_E4M3) {
@@ -362,13 +370,13 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
 }
 
 template <int kN>
-int launch_n(const TcArgs &a, int sms, int64_t ntiles, cudaStream_t st) {
+int launch_n(const TcArgs &a, int sms, int64_t ntiles, cudaStream_t st, bool acc16) {
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   const size_t smem = TileCfg<kN>::kSmem;
   void (*kern)(TcArgs);
   switch (a.dt) {
   case GLM_BF16: kern = k_gram_tc<GLM_BF16, kN>; break;
-  case GLM_F16: kern = k_gram_tc<GLM_F16, kN>; break;
+  case GLM_F16: kern = acc16 ? k_gram_tc<GLM_F16, kN, true> : k_gram_tc<GLM_F16, kN>; break;
   case GLM_TF32: kern = k_gram_tc<GLM_TF32, kN>; break;
   default: kern = k_gram_tc<GLM_E4M3, kN>; break;
   }
@@ -386,8 +394,12 @@ bool gram_tc_supported(int dt, int64_t ld) {
   return false;
 }
 
-int launch_gram_tc(const GramArgs &g, cudaStream_t st) {
+namespace {
+
+int launch_gram_tc_impl(const GramArgs &g, cudaStream_t st, bool acc16) {
   if (g.s < 2 || g.nouter <= 0) return GLM_OK;
+  if (acc16 && g.dt != GLM_F16)
+    return set_error(GLM_EINVAL, "tcgen05 Gram with FP16 accumulation needs F16 operands");
   if (!gram_tc_supported(g.dt, g.ld))
     return set_error(GLM_EUNSUPPORTED, "tcgen05 Gram: unsupported operand type or ld");
   TcArgs a;
@@ -414,8 +426,16 @@ int launch_gram_tc(const GramArgs &g, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // wide tiles unless they would leave SMs idle (few, long-K tiles)
   const int64_t wide = g.nouter * tiles_per_outer<256>(sb);
-  if (wide >= sms) return launch_n<256>(a, sms, wide, st);
-  return launch_n<128>(a, sms, g.nouter * tiles_per_outer<128>(sb), st);
+  if (wide >= sms) return launch_n<256>(a, sms, wide, st, acc16);
+  return launch_n<128>(a, sms, g.nouter * tiles_per_outer<128>(sb), st, acc16);
+}
+
+}  // namespace
+
+int launch_gram_tc(const GramArgs &g, cudaStream_t st) { return launch_gram_tc_impl(g, st, false); }
+
+int launch_gram_tc_f16acc(const GramArgs &g, cudaStream_t st) {
+  return launch_gram_tc_impl(g, st, true);
 }
 
 }  // namespace glm

@@ -62,14 +62,16 @@ class glm_ca_opts(ctypes.Structure):
                 ("first_iter", ctypes.c_int64), ("problem", ctypes.c_uint32),
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("chunk_outer", ctypes.c_int64), ("gram_impl", ctypes.c_int),
-                ("timing", ctypes.c_int), ("wait_probe_cycles", ctypes.c_int64)]
+                ("timing", ctypes.c_int), ("chain_impl", ctypes.c_int),
+                ("wait_probe_cycles", ctypes.c_int64)]
 
 
 class glm_run_plan(ctypes.Structure):
     _fields_ = [("chunk_outer", ctypes.c_int64), ("chunks", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("cluster", ctypes.c_int),
                 ("gram_impl", ctypes.c_int), ("gram_dtype", ctypes.c_int),
-                ("gemv_dtype", ctypes.c_int), ("recurrence_f64", ctypes.c_int)]
+                ("gemv_dtype", ctypes.c_int), ("recurrence_f64", ctypes.c_int),
+                ("chain_impl", ctypes.c_int)]
 
 
 class glm_problem_desc(ctypes.Structure):

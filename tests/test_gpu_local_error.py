@@ -52,14 +52,15 @@ U32, U64 = 2.0 ** -24, 2.0 ** -53
 U_IN = {"f32": 0.0, "tf32": 2.0 ** -11, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
 
 # (storage, Gram and GEMV operands, s, FP64 recurrence, Gram implementation:
-# 0 automatic, 3 FP16 accumulation)
+# 0 automatic, 3 FP16 accumulation (SIMT), 4 FP16 accumulation (tcgen05))
 MODES = [("f32", "f32", 8, 0, 0), ("f32", "tf32", 8, 0, 0), ("f32", "bf16", 8, 0, 0),
          ("f32", "f16", 8, 0, 0), ("bf16", "bf16", 8, 0, 0), ("f32", "f32", 32, 1, 0),
          ("f32", "bf16", 32, 1, 0), ("f32", "f32", 16, 0, 0),
-         pytest.param("f32", "f16", 8, 0, 3, id="f16acc")]
+         pytest.param("f32", "f16", 8, 0, 3, id="f16acc"),
+         pytest.param("f32", "f16", 8, 0, 4, id="f16acc-tc")]
 
 # (loss, Gram implementation) the theorem's hypotheses exclude at this shape
-EXCLUDED = {("lsq", 3)}
+EXCLUDED = {("lsq", 3), ("lsq", 4)}
 
 
 @pytest.fixture(scope="module")
@@ -114,7 +115,7 @@ def test_one_outer_step_within_theorem_budget(case, storage, op, s, rec, impl):
     ev = le.local_error(Y, yI, x0.astype(np.float64), loss, ETA, s, B,
                         u_A=2.0 ** -8 if storage == "bf16" else 0.0,
                         gamma_r=le.gamma_mixed(N, u_in, U32),
-                        gamma_G=le.gamma_mixed(N, u_in, 2.0 ** -11 if impl == 3 else U32),
+                        gamma_G=le.gamma_mixed(N, u_in, 2.0 ** -11 if impl in (3, 4) else U32),
                         u_c=U64 if rec else U32, u_sigma=U32,
                         gamma_g=le.gamma_mixed(s * B, u_in, U32), u_x=U32,
                         C_delta=C_delta)

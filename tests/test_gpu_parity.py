@@ -274,11 +274,14 @@ def test_gram_lower_bound(G, dt, impl, nouter, s, b, n):
         assert np.all(err <= bound), (dt, impl, float(np.max(err - bound)))
 
 
-@pytest.mark.parametrize("nouter,s,b,n", [(3, 4, 16, 100), (2, 16, 64, 512), (1, 3, 130, 70)])
-def test_gram_lower_f16acc_bound(G, nouter, s, b, n):
-    # Recipe F's Gram slot: FP16 operands and FP16 accumulation by fused
-    # half multiply-adds, one rounding per step: |G^ - G| <= gamma_n(2^-11)
-    # |Y| |Y|^T entrywise (valid while n 2^-11 < 1)
+@pytest.mark.parametrize("impl", [3, 4])
+@pytest.mark.parametrize("nouter,s,b,n", [(3, 4, 16, 100), (2, 16, 64, 512), (1, 3, 130, 70),
+                                          (1, 8, 64, 1000)])
+def test_gram_lower_f16acc_bound(G, nouter, s, b, n, impl):
+    # Recipe F's Gram slot: FP16 operands and FP16 accumulation (3: fused
+    # half multiply-adds, one rounding per step; 4: tcgen05 with an FP16
+    # accumulator, at most one rounding per step as well): |G^ - G| <=
+    # gamma_n(2^-11) |Y| |Y|^T entrywise (valid while n 2^-11 < 1)
     rng = np.random.default_rng(s * 1000 + b + n + 7)
     sb = s * b
     ld = ((n + 63) // 64) * 64
@@ -288,7 +291,7 @@ def test_gram_lower_f16acc_bound(G, nouter, s, b, n):
     Yd = torch.from_numpy(dev).to(torch.float16).cuda()
     Gd = torch.full((nouter * _gram_size(s, b),), float("nan"), dtype=torch.float32,
                     device="cuda")
-    G.glm_gram_lower(Yd, G.GLM_F16, nouter, s, b, n, ld, None, Gd, 3)
+    G.glm_gram_lower(Yd, G.GLM_F16, nouter, s, b, n, ld, None, Gd, impl)
     torch.cuda.synchronize()
     got = _unpack_gram(Gd.cpu().numpy().astype(np.float64), nouter, s, b)
     u = 2.0 ** -11
