@@ -95,7 +95,7 @@ __host__ __device__ inline SLayout stream_layout(int64_t n, int64_t b, int s, in
   L.off_rown = take((size_t)s * L.rpb * tr, 16);
   L.off_yown = take((size_t)s * L.rpb * 4, 16);
   L.off_part = take((size_t)L.ngrp * L.nc * 4, 16);
-  L.off_bar = take((size_t)(1 + s + 6 * kMaxRing) * 8, 16);
+  L.off_bar = take((size_t)(2 + s + 6 * kMaxRing) * 8, 16);  // x, u[s], rings, probe
   L.off_coef = take((size_t)3 * (s + 1) * tr, 16);
   L.off_rem = take((size_t)4 * 16 * 4, 16);
   const size_t fixed = (off + 1023) / 1024 * 1024;
@@ -109,7 +109,7 @@ __host__ __device__ inline SLayout stream_layout(int64_t n, int64_t b, int s, in
   for (int q = 0; q < 12 && !L.slot; ++q) {
     const size_t sl = (size_t)cand[q][3] * 1024;
     const int nr = cand[q][0] + cand[q][1] + cand[q][2];
-    if (fixed + (size_t)nr * sl <= kSmemMax) {
+    if (fixed + (size_t)nr * sl + 1024 <= kSmemMax) {
       L.slot = sl;
       L.NM = cand[q][0];
       L.NU = cand[q][1];
@@ -346,8 +346,8 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
   const uint32_t emptyU = fullU + 8 * kMaxRing;
   const uint32_t fullG = emptyU + 8 * kMaxRing;
   const uint32_t emptyG = fullG + 8 * kMaxRing;
+  const uint32_t probe_bar = emptyG + 8 * kMaxRing;     // never signalled
   __shared__ int s_abort;
-  __shared__ uint32_t s_probe_bar[2];
   __shared__ int s_fills[3];  // fills issued per ring (M, U, G)
 
   // row warps: groups of four own rows
@@ -365,7 +365,7 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
       mbar_init(fullG + 8 * k, 1);
       mbar_init(emptyG + 8 * k, nrw > 0 ? nrw : 1);
     }
-    mbar_init(smem_u32(&s_probe_bar[0]), 1);
+    mbar_init(probe_bar, 1);
     fence_mbar_init_cluster();
     s_abort = 0;
     s_fills[0] = s_fills[1] = s_fills[2] = 0;
@@ -389,7 +389,7 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
 
   bool abort = false;
   if (a.probe > 0) {  // failure-path probe, agreed by the cluster before any exchange
-    if (tid == 0 && !mbar_wait_bounded(smem_u32(&s_probe_bar[0]), 0, a.probe))
+    if (tid == 0 && !mbar_wait_bounded(probe_bar, 0, a.probe))
       atomicOr(&s_abort, 1);
     cluster.sync();
     int any = 0;
@@ -780,7 +780,7 @@ bool chain_stream_ok(const ChainArgs &a) {
   if (a.cluster < 1 || a.cluster > 16) return false;
   const SLayout L = layout_of(a);
   return L.slot > 0 && L.rpb <= 32 && L.nc <= 256 && L.TM >= 1 && L.TU >= 1 &&
-         (a.s < 2 || L.PC >= 4) && L.total <= kSmemMax + 1024 && a.s <= 256;
+         (a.s < 2 || L.PC >= 4) && L.total <= kSmemMax && a.s <= 256;
 }
 
 int launch_chain_stream(const ChainArgs &a, cudaStream_t st) {
