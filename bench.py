@@ -337,7 +337,8 @@ def leg(ds, stream, torch, glm, peaks, clocks, *, name, s, b, eta, lam, T, seed,
     plan = glm.glm_ca_plan(ds.h, s, b, eta, lam, T, glm.default_ca_opts(**o))
     r = {"workload": name, "value": T * b / (ms / 1e3), "unit": "samples/s", "ms_per_run": ms,
          "s": s, "b": b, "eta": eta, "lambda": lam, "iters": T, "gram_dtype": gram,
-         "recurrence": "f64" if plan.recurrence_f64 else "f32", "gram_impl": plan.gram_impl,
+         "recurrence": {0: "f32", 1: "f64", 2: "compensated f32"}[plan.recurrence_f64],
+         "gram_impl": plan.gram_impl, "chain": {1: "resident", 2: "streaming"}[plan.chain_impl],
          "cluster": plan.cluster, "launches_per_run": plan.launches,
          "final_loss": ds.loss_value(x, lam)}
     r["roofline"] = roofline(kms, kl, ms, T, s, b, n, e_A, gram, peaks, clocks,
@@ -364,8 +365,9 @@ def wide_legs(args, torch, synth, glm, peaks, clocks):
     out = []
     for st, gram, s, rec in [("bf16", "bf16", 16, -1), ("bf16", "e4m3", 16, -1),
                              ("bf16", "f32", 16, -1), ("f16", "f16", 16, -1),
-                             ("bf16", "bf16", 32, 1), ("bf16", "bf16", 32, 0),
-                             ("bf16", "bf16", 64, 1), ("bf16", "bf16", 64, 0)]:
+                             ("bf16", "bf16", 32, 1), ("bf16", "bf16", 32, 2),
+                             ("bf16", "bf16", 32, 0), ("bf16", "bf16", 64, 1),
+                             ("bf16", "bf16", 64, 2), ("bf16", "bf16", 64, 0)]:
         r = leg(ds[st], stream, torch, glm, peaks, clocks, name=f"wide 400000x2048 {st} storage",
                 s=s, e_A=2, gram=gram, recurrence_f64=rec, reps=1, **common)
         r["storage"] = st
@@ -388,7 +390,7 @@ def large_legs(args, torch, synth, glm, peaks, clocks):
     del A, y
     x = torch.zeros(1024, dtype=torch.float32, device="cuda")
     out = []
-    for rec in (1, 0):
+    for rec in (1, 2, 0):
         r = leg(ds, stream, torch, glm, peaks, clocks, name="large lsq 4194304x1024 bf16",
                 s=64, b=256, eta=50.0, lam=1e-5, T=65536, seed=0, e_A=2, gram="bf16", n=1024,
                 x=x, recurrence_f64=rec, reps=1)

@@ -156,7 +156,8 @@ typedef struct {
                          cluster's shared memory), 2 streaming (Y and G
                          streamed through shared-memory rings: wide rows,
                          long blocks).  Automatic takes the streaming kernel
-                         when the resident one cannot stage the step, or for
+                         when the resident one cannot stage the step (except
+                         with FP64 sums, which stay resident), and for
                          recurrence_f64 = 2.                                  */
   int64_t wait_probe_cycles;
                       /* Failure-path test hook; 0 (default) = off.  When > 0,

@@ -161,22 +161,28 @@ template <> struct Raw8s<__half> {
   }
 };
 
+// Bounded wait; after 64 back-to-back probes a waiter off the critical path
+// (nap > 0) sleeps `nap` ns between probes, so that a dozen waiting warps do
+// not crowd the shared-memory pipe the rings' copies and the recurrence use.
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
-                                              const volatile int *abort_flag) {
+                                              const volatile int *abort_flag,
+                                              unsigned nap = 0) {
   if (mbar_test_wait(bar, parity)) return true;
   const long long t0 = clock64();
   for (unsigned k = 1;; ++k) {
     if (mbar_test_wait(bar, parity)) return true;
     if ((k & 31) == 0 && (*abort_flag || clock64() - t0 > kWaitBudget)) return false;
+    if (nap && k > 64) __nanosleep(nap);
   }
 }
 
-// lane-polled wait shared with the warp; false on timeout / abort
+// Warp-uniform wait: every lane probes the barrier (one broadcast read), so
+// the loop does not diverge; the outcome is made uniform before returning.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int lane,
-                                          const volatile int *ab) {
-  int ok = 1;
-  if (lane == 0) ok = wait_or_abort(bar, parity, ab);
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+                                          const volatile int *ab, unsigned nap = 0) {
+  (void)lane;
+  const bool ok = wait_or_abort(bar, parity, ab, nap);
+  return __all_sync(0xffffffffu, ok);
 }
 
 // Barrier of the consumer warps (named barrier 1) that also ORs a predicate
@@ -317,27 +323,51 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
   const int s = a.s;
   const int64_t sb = (int64_t)s * b;
   const SLayout L = stream_layout(n, b, s, C, (int)sizeof(TY), (int)sizeof(TH), a.ldy);
-  const int rpb = L.rpb, nc = L.nc;
+  const int L_NG = L.NG;
+  const int L_NM = L.NM;
+  const int L_NU = L.NU;
+  const int L_PC = L.PC;
+  const int L_TM = L.TM;
+  const int L_TU = L.TU;
+  const int L_V = L.V;
+  const int L_mbox = L.mbox;
+  const int L_mbw = L.mbw;
+  const int L_mshift = L.mshift;
+  const int L_nc = L.nc;
+  const int L_ngrp = L.ngrp;
+  const int L_npad = L.npad;
+  const size_t L_off_bar = L.off_bar;
+  const size_t L_off_coef = L.off_coef;
+  const size_t L_off_part = L.off_part;
+  const size_t L_off_rem = L.off_rem;
+  const size_t L_off_ring = L.off_ring;
+  const size_t L_off_rown = L.off_rown;
+  const size_t L_off_uh = L.off_uh;
+  const size_t L_off_x = L.off_x;
+  const size_t L_off_yown = L.off_yown;
+  const int L_rpb = L.rpb;
+  const size_t L_slot = L.slot;
+  const int rpb = L_rpb, nc = L_nc;
   const int64_t l0 = (int64_t)rank * rpb;
   const int nown = (int)max((int64_t)0, min((int64_t)rpb, b - l0));
   const int64_t col0 = (int64_t)rank * nc;
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  float *xf = reinterpret_cast<float *>(smem + L.off_x);
-  TH *uh = reinterpret_cast<TH *>(smem + L.off_uh);
-  TH *rown = reinterpret_cast<TH *>(smem + L.off_rown);
-  float *yown = reinterpret_cast<float *>(smem + L.off_yown);
-  float *part = reinterpret_cast<float *>(smem + L.off_part);
-  TH *cpw = reinterpret_cast<TH *>(smem + L.off_coef);
+  float *xf = reinterpret_cast<float *>(smem + L_off_x);
+  TH *uh = reinterpret_cast<TH *>(smem + L_off_uh);
+  TH *rown = reinterpret_cast<TH *>(smem + L_off_rown);
+  float *yown = reinterpret_cast<float *>(smem + L_off_yown);
+  float *part = reinterpret_cast<float *>(smem + L_off_part);
+  TH *cpw = reinterpret_cast<TH *>(smem + L_off_coef);
   TH *cinw = cpw + (s + 1);
   TH *zcw = cinw + (s + 1);
-  uint32_t *rem = reinterpret_cast<uint32_t *>(smem + L.off_rem);
+  uint32_t *rem = reinterpret_cast<uint32_t *>(smem + L_off_rem);
   const uint32_t sbase = smem_u32(smem);
-  unsigned char *ring = smem + (round_up(sbase + L.off_ring, 1024) - sbase);
+  unsigned char *ring = smem + (round_up(sbase + L_off_ring, 1024) - sbase);
   unsigned char *ringM = ring;
-  unsigned char *ringU = ringM + (size_t)L.NM * L.slot;
-  unsigned char *ringG = ringU + (size_t)L.NU * L.slot;
-  const uint32_t bar0 = smem_u32(smem + L.off_bar);
+  unsigned char *ringU = ringM + (size_t)L_NM * L_slot;
+  unsigned char *ringG = ringU + (size_t)L_NU * L_slot;
+  const uint32_t bar0 = smem_u32(smem + L_off_bar);
   const uint32_t bar_x = bar0;
   const uint32_t bar_u = bar0 + 8;                       // + 8 j, j < s
   const uint32_t fullM = bar0 + 8 * (1 + s);             // + 8 k
@@ -384,7 +414,7 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
     rem[32 + tid] = mapa(smem_u32(xf), tid);
     rem[48 + tid] = mapa(bar_x, tid);
   }
-  for (int64_t c = tid; c < L.npad; c += kThreads) xf[c] = c < n ? a.x[c] : 0.f;
+  for (int64_t c = tid; c < L_npad; c += kThreads) xf[c] = c < n ? a.x[c] : 0.f;
   cluster.sync();
 
   bool abort = false;
@@ -403,113 +433,168 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
     cluster.sync();
   }
   const volatile int *vab = &s_abort;
-  const int mt_per_blk = (nown + L.TM - 1) / max(L.TM, 1);     // margin tiles per block
-  const int ut_per_blk = (int)((b + L.TU - 1) / max(L.TU, 1));  // update tiles per block
+  const int mt_per_blk = (nown + L_TM - 1) / max(L_TM, 1);     // margin tiles per block
+  const int ut_per_blk = (int)((b + L_TU - 1) / max(L_TU, 1));  // update tiles per block
   const int gsz = (int)gram_size(s, b);
 
   if (warp == kProducer) {
     // ===================== producer ===================================
-    if (lane == 0 && !abort) {
+    if (!abort) {
+      // The whole warp runs the loop in lockstep (every lane keeps the same
+      // cursors); lane 0 owns the barrier operations and the lanes issue a
+      // piece's row copies and a margin tile's boxes side by side.
       // cursors: outer step, block, tile / piece of each ring's sequence
       int mh = 0, mj = 0, mt = 0, mk = 0;           // M: step, block, tile, fill count
       int uhh = 0, uj = 0, ut = 0, uk = 0;
       int gh = 0, gj = 1, gp = 0, gk = 0;
       auto shof = [&](int hh) { return hh == a.nouter - 1 ? a.s_last : s; };
-      auto skipG = [&]() {  // advance to the next step that has block rows >= 1
+      // G cursor kept incrementally (no per-piece offset sums or divisions):
+      // first float of this CTA's own rows of block row gj of step gh, the
+      // row stride, the block row's width, the slot and its phase
+      const float *grow = nullptr;
+      int64_t gld = 0, gjb = 0;
+      int gslot = 0;
+      uint32_t gphase = 0;
+      auto gstart = [&]() {  // (re)position at (gh, gj); skip steps without block rows >= 1
         while (gh < a.nouter && gj >= shof(gh)) { ++gh; gj = 1; gp = 0; }
+        if (gh < a.nouter) {
+          gjb = (int64_t)gj * b;
+          gld = gram_ld(gj, b);
+          grow = a.G + (int64_t)gh * gsz + gram_off(gj, b) + l0 * gld;
+        }
       };
-      skipG();
+      gstart();
       if (nown == 0) { mh = a.nouter; gh = a.nouter; }
-      const uint32_t mbytes = (uint32_t)((size_t)L.mbox * L.mbw * L.TM * sizeof(TY));
-      const uint32_t ubytes = (uint32_t)((size_t)nc * L.TU * sizeof(TY));
+      const uint32_t mbytes = (uint32_t)((size_t)L_mbox * L_mbw * L_TM * sizeof(TY));
+      const uint32_t mboxb = (uint32_t)((size_t)L_mbw * L_TM * sizeof(TY));
+      const uint32_t ubytes = (uint32_t)((size_t)nc * L_TU * sizeof(TY));
+      int uslot = 0, mslot = 0;
+      uint32_t uphase = 0, mphase = 0;
+      int32_t uy = 0, my = (int32_t)l0;   // first row of the next update / margin tile
       long long last = clock64();
       while (mh < a.nouter || uhh < a.nouter || gh < a.nouter) {
         bool did = false;
         // G pieces first: the recurrence's critical path
-        if (gh < a.nouter) {
-          const int slot = gk % L.NG;
-          if (gk < L.NG || mbar_test_wait(emptyG + 8 * slot, (uint32_t)((gk / L.NG - 1) & 1))) {
-            const int64_t jb = (int64_t)gj * b, ldj = gram_ld(gj, b);
-            const int64_t c0 = (int64_t)gp * L.PC;
-            const int64_t w = min((int64_t)L.PC, jb - c0);
-            const uint32_t wb = (uint32_t)(round_up(w, 4) * 4);
-            const uint32_t dst = smem_u32(ringG + (size_t)slot * L.slot);
-            const uint32_t full = fullG + 8 * slot;
-            mbar_arrive_expect_tx(full, wb * (uint32_t)nown);
-            const float *src = a.G + (int64_t)gh * gsz + gram_off(gj, b) + l0 * ldj + c0;
-            for (int r = 0; r < nown; ++r)
-              bulk_load(dst + (uint32_t)(r * L.PC * 4), src + (int64_t)r * ldj, wb, full);
-            ++gk;
-            did = true;
-            if (c0 + w >= jb) { ++gj; gp = 0; skipG(); } else { ++gp; }
+        int fr = 0;
+        if (lane == 0)
+          fr = (gh < a.nouter && (gk < L_NG || mbar_test_wait(emptyG + 8 * gslot, gphase ^ 1u)))
+               | ((uhh < a.nouter && (uk < L_NU || mbar_test_wait(emptyU + 8 * uslot, uphase ^ 1u)))
+                  << 1)
+               | ((mh < a.nouter && (mk < L_NM || mbar_test_wait(emptyM + 8 * mslot, mphase ^ 1u)))
+                  << 2);
+        fr = __shfl_sync(0xffffffffu, fr, 0);
+        if (fr & 1) {
+          const int64_t c0 = (int64_t)gp * L_PC;
+          const int64_t w = min((int64_t)L_PC, gjb - c0);
+          const uint32_t wb = (uint32_t)(round_up(w, 4) * 4);
+          const uint32_t dst = smem_u32(ringG + (size_t)gslot * L_slot);
+          const uint32_t full = fullG + 8 * gslot;
+          if (lane == 0) mbar_arrive_expect_tx(full, wb * (uint32_t)nown);
+          __syncwarp();
+          if (lane < nown)  // one row of the piece per lane
+            bulk_load(dst + (uint32_t)(lane * L_PC * 4), grow + c0 + (int64_t)lane * gld, wb, full);
+          ++gk;
+          if (++gslot == L_NG) { gslot = 0; gphase ^= 1u; }
+          did = true;
+          if (c0 + w >= gjb) {
+            // next block row: its offset follows this one's b rows of gld floats
+            grow += (int64_t)b * gld - l0 * gld;
+            ++gj;
+            gp = 0;
+            if (gj < shof(gh)) {
+              gjb = (int64_t)gj * b;
+              gld = gram_ld(gj, b);
+              grow += l0 * gld;
+            } else {
+              ++gh;
+              gj = 1;
+              gstart();
+            }
+          } else {
+            ++gp;
           }
         }
-        if (uhh < a.nouter) {
-          const int slot = uk % L.NU;
-          if (uk < L.NU || mbar_test_wait(emptyU + 8 * slot, (uint32_t)((uk / L.NU - 1) & 1))) {
-            const uint32_t full = fullU + 8 * slot;
+        if (fr & 2) {
+          const uint32_t full = fullU + 8 * uslot;
+          if (lane == 0) {
             mbar_arrive_expect_tx(full, ubytes);
-            tma_load_2d(smem_u32(ringU + (size_t)slot * L.slot), &a.umap, (int32_t)col0,
-                        (int32_t)((int64_t)uhh * sb + (int64_t)uj * b + (int64_t)ut * L.TU), full);
-            ++uk;
-            did = true;
-            if (++ut == ut_per_blk) { ut = 0; if (++uj == shof(uhh)) { uj = 0; ++uhh; } }
+            tma_load_2d(smem_u32(ringU + (size_t)uslot * L_slot), &a.umap, (int32_t)col0, uy, full);
+          }
+          ++uk;
+          if (++uslot == L_NU) { uslot = 0; uphase ^= 1u; }
+          did = true;
+          uy += L_TU;
+          if (++ut == ut_per_blk) {
+            ut = 0;
+            if (++uj == shof(uhh)) { uj = 0; ++uhh; }
+            uy = (int32_t)((int64_t)uhh * sb + (int64_t)uj * b);
           }
         }
-        if (mh < a.nouter) {
-          const int slot = mk % L.NM;
-          if (mk < L.NM || mbar_test_wait(emptyM + 8 * slot, (uint32_t)((mk / L.NM - 1) & 1))) {
-            const uint32_t full = fullM + 8 * slot;
-            mbar_arrive_expect_tx(full, mbytes);
-            const uint32_t dst = smem_u32(ringM + (size_t)slot * L.slot);
-            const int32_t y = (int32_t)((int64_t)mh * sb + (int64_t)mj * b + l0 + (int64_t)mt * L.TM);
-            for (int k = 0; k < L.mbox; ++k)
-              tma_load_2d(dst + (uint32_t)((size_t)k * L.mbw * L.TM * sizeof(TY)), &a.mmap,
-                          k * L.mbw, y, full);
-            ++mk;
-            did = true;
-            if (++mt == mt_per_blk) { mt = 0; if (++mj == shof(mh)) { mj = 0; ++mh; } }
+        if (fr & 4) {
+          const uint32_t full = fullM + 8 * mslot;
+          if (lane == 0) mbar_arrive_expect_tx(full, mbytes);
+          __syncwarp();
+          const uint32_t dst = smem_u32(ringM + (size_t)mslot * L_slot);
+          if (lane < L_mbox)  // one box of the tile per lane
+            tma_load_2d(dst + (uint32_t)lane * mboxb, &a.mmap, lane * L_mbw, my, full);
+          ++mk;
+          if (++mslot == L_NM) { mslot = 0; mphase ^= 1u; }
+          did = true;
+          my += L_TM;
+          if (++mt == mt_per_blk) {
+            mt = 0;
+            if (++mj == shof(mh)) { mj = 0; ++mh; }
+            my = (int32_t)((int64_t)mh * sb + (int64_t)mj * b + l0);
           }
         }
         if (did) {
           last = clock64();
-        } else if (*vab || clock64() - last > kWaitBudget) {
-          atomicOr(&s_abort, 1);
-          break;
+        } else {
+          int give_up = 0;
+          if (lane == 0) give_up = *vab || clock64() - last > kWaitBudget;
+          if (__shfl_sync(0xffffffffu, give_up, 0)) {
+            if (lane == 0) atomicOr(&s_abort, 1);
+            break;
+          }
+          __nanosleep(200);  // nothing to refill: leave the issue slots to the consumers
         }
       }
-      s_fills[0] = mk;
-      s_fills[1] = uk;
-      s_fills[2] = gk;
+      if (lane == 0) {
+        s_fills[0] = mk;
+        s_fills[1] = uk;
+        s_fills[2] = gk;
+      }
     }
   } else if (!abort) {
     // ===================== consumers ==================================
     int mk = 0, uk = 0, gk = 0;  // fills consumed per ring (same sequences)
+    int cms = 0, cus = 0, cgs = 0;           // their slots
+    uint32_t cmp_ = 0, cup = 0, cgp = 0;     // and phase parities
     const int ct = tid;          // 0 .. 479
     // update assignment: worker thread -> (8-column vector v, row group g)
     const int wt = tid - kRowW * 32;                   // 0 .. 351 for workers
-    const int ev = wt >= 0 ? wt % max(L.V, 1) : 0;
-    const int eg = wt >= 0 ? wt / max(L.V, 1) : 0;
+    const int ev = wt >= 0 ? wt % max(L_V, 1) : 0;
+    const int eg = wt >= 0 ? wt / max(L_V, 1) : 0;
     for (int h = 0; h < a.nouter; ++h) {
       const int sh = (h == a.nouter - 1) ? a.s_last : s;
       const float *labh = a.ylab + (int64_t)h * a.sbp;
       // ---- margins of own rows (full width) ------------------------------
-      bool ok = h == 0 || warp_wait(bar_x, (uint32_t)((h - 1) & 1), lane, vab);
+      bool ok = h == 0 || warp_wait(bar_x, (uint32_t)((h - 1) & 1), lane, vab, 32);
       for (int j = 0; j < sh && ok && nown > 0; ++j) {
         for (int t = 0; t < mt_per_blk; ++t) {
-          const int slot = mk % L.NM;
-          if (!warp_wait(fullM + 8 * slot, (uint32_t)((mk / L.NM) & 1), lane, vab)) {
+          const int slot = cms;
+          if (!warp_wait(fullM + 8 * slot, cmp_, lane, vab, 32)) {
             ok = false;
             break;
           }
-          const TY *tile = reinterpret_cast<const TY *>(ringM + (size_t)slot * L.slot);
-          const int r_end = min(L.TM, nown - t * L.TM);
+          const TY *tile = reinterpret_cast<const TY *>(ringM + (size_t)slot * L_slot);
+          const int r_end = min(L_TM, nown - t * L_TM);
           for (int r = warp; r < r_end; r += kCons) {
             float acc = 0.f;
             for (int c = lane * 8; c < (int)n; c += 256) {
               float v[8];
-              Raw8s<TY>::get(tile + ((size_t)(c >> L.mshift) * L.TM + r) * L.mbw +
-                                 (c & (L.mbw - 1)), v);
+              Raw8s<TY>::get(tile + ((size_t)(c >> L_mshift) * L_TM + r) * L_mbw +
+                                 (c & (L_mbw - 1)), v);
               const float4 x0 = *reinterpret_cast<const float4 *>(xf + c);
               const float4 x1 = *reinterpret_cast<const float4 *>(xf + c + 4);
               acc = fmaf(v[0], x0.x, acc); acc = fmaf(v[1], x0.y, acc);
@@ -520,7 +605,7 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if (lane == 0) {
-              const int q = t * L.TM + r;
+              const int q = t * L_TM + r;
               rown[j * rpb + q] = (TH)acc;
               yown[j * rpb + q] = labh[(int64_t)j * b + l0 + q];
             }
@@ -528,9 +613,10 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
           __syncwarp();
           if (lane == 0) mbar_arrive(emptyM + 8 * slot);
           ++mk;
+          if (++cms == L_NM) { cms = 0; cmp_ ^= 1u; }
         }
       }
-      if (tid == 0 && ok) mbar_arrive_expect_tx(bar_x, (uint32_t)(L.npad * 4));  // this step's x
+      if (tid == 0 && ok) mbar_arrive_expect_tx(bar_x, (uint32_t)(L_npad * 4));  // this step's x
       if (consumers_or(!ok || *vab)) {  // own margins complete (or give up together)
         atomicOr(&s_abort, 1);
         break;
@@ -541,33 +627,38 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
         const int rw = warp;
         for (int j = 0; j < sh && ok; ++j) {
           const int64_t jb = (int64_t)j * b;
-          const int npieces = j > 0 ? (int)((jb + L.PC - 1) / L.PC) : 0;
+          const int npieces = j > 0 ? (int)((jb + L_PC - 1) / L_PC) : 0;
           // accumulators for this warp's groups (up to two groups of four rows)
           DotAcc<MODE> acc[2];
           acc[0].zero();
           acc[1].zero();
           bool waited = j == 0;  // block j - 1's residuals landed (j = 0: none needed)
           for (int p = 0; p < npieces; ++p) {
-            const int64_t c0 = (int64_t)p * L.PC;
-            const int w = (int)min((int64_t)L.PC, jb - c0);
+            const int64_t c0 = (int64_t)p * L_PC;
+            const int w = (int)min((int64_t)L_PC, jb - c0);
             if (!waited && c0 + w > jb - b) {  // the piece reaches block j - 1
               if (!warp_wait(bar_u + 8 * (j - 1), upar, lane, vab)) { ok = false; break; }
               waited = true;
             }
-            const int slot = gk % L.NG;
+            const int slot = cgs;
             if (rw < nrw) {
-              if (!warp_wait(fullG + 8 * slot, (uint32_t)((gk / L.NG) & 1), lane, vab)) {
+              if (!warp_wait(fullG + 8 * slot, cgp, lane, vab)) {
                 ok = false;
                 break;
               }
-              const float *gp = reinterpret_cast<const float *>(ringG + (size_t)slot * L.slot);
-              for (int gi = 0, q0 = 4 * rw; q0 < nown && gi < 2; ++gi, q0 += 4 * kRowW)
-                piece_dot4<MODE, TH>(gp + (size_t)q0 * L.PC, L.PC, min(4, nown - q0), uh + c0,
-                                     w, lane, acc[gi]);
+              const float *gp = reinterpret_cast<const float *>(ringG + (size_t)slot * L_slot);
+#pragma unroll
+              for (int gi = 0; gi < 2; ++gi) {  // constant indices keep acc in registers
+                const int q0 = 4 * rw + 4 * kRowW * gi;
+                if (q0 < nown)
+                  piece_dot4<MODE, TH>(gp + (size_t)q0 * L_PC, L_PC, min(4, nown - q0), uh + c0,
+                                       w, lane, acc[gi]);
+              }
               __syncwarp();
               if (lane == 0) mbar_arrive(emptyG + 8 * slot);
             }
             ++gk;
+            if (++cgs == L_NG) { cgs = 0; cgp ^= 1u; }
           }
           if (!ok) break;
           if (j >= 1 && !waited) {
@@ -575,7 +666,10 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
           }
           if (rw < nrw) {
             const TH cj = cpw[j], zj = zcw[j], ij = cinw[j];
-            for (int gi = 0, q0 = 4 * rw; q0 < nown && gi < 2; ++gi, q0 += 4 * kRowW) {
+#pragma unroll
+            for (int gi = 0; gi < 2; ++gi) {
+              const int q0 = 4 * rw + 4 * kRowW * gi;
+              if (q0 >= nown) continue;
               const int nq = min(4, nown - q0);
               const int q = lane >> 3;
               const int rq = q0 + (q < nq ? q : nq - 1);
@@ -632,20 +726,20 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) { accv[i] = 0.f; cmp[i] = 0.f; }
         for (int j = 0; j < sh && ok; ++j) {
-          if (!warp_wait(bar_u + 8 * j, upar, lane, vab)) { ok = false; break; }
+          if (!warp_wait(bar_u + 8 * j, upar, lane, vab, 256)) { ok = false; break; }
           for (int t = 0; t < ut_per_blk; ++t) {
-            const int slot = uk % L.NU;
-            if (!warp_wait(fullU + 8 * slot, (uint32_t)((uk / L.NU) & 1), lane, vab)) {
+            const int slot = cus;
+            if (!warp_wait(fullU + 8 * slot, cup, lane, vab, 256)) {
               ok = false;
               break;
             }
-            const TY *tile = reinterpret_cast<const TY *>(ringU + (size_t)slot * L.slot);
-            const int r_end = (int)min((int64_t)L.TU, b - (int64_t)t * L.TU);
-            if (eg < L.ngrp && col0 + ev * 8 < n) {
-              for (int r = eg; r < r_end; r += L.ngrp) {
+            const TY *tile = reinterpret_cast<const TY *>(ringU + (size_t)slot * L_slot);
+            const int r_end = (int)min((int64_t)L_TU, b - (int64_t)t * L_TU);
+            if (eg < L_ngrp && col0 + ev * 8 < n) {
+              for (int r = eg; r < r_end; r += L_ngrp) {
                 float f[8];
                 Raw8s<TY>::get(tile + (size_t)r * nc + ev * 8, f);
-                const float wv = (float)uh[(int64_t)j * b + (int64_t)t * L.TU + r];
+                const float wv = (float)uh[(int64_t)j * b + (int64_t)t * L_TU + r];
                 if (a.kahan) {
 #pragma unroll
                   for (int i = 0; i < 8; ++i) {
@@ -663,9 +757,10 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
             __syncwarp();
             if (lane == 0) mbar_arrive(emptyU + 8 * slot);
             ++uk;
+            if (++cus == L_NU) { cus = 0; cup ^= 1u; }
           }
         }
-        if (eg < L.ngrp) {
+        if (eg < L_ngrp) {
           float4 *pp = reinterpret_cast<float4 *>(part + (size_t)eg * nc + ev * 8);
           pp[0] = make_float4(accv[0] - cmp[0], accv[1] - cmp[1], accv[2] - cmp[2], accv[3] - cmp[3]);
           pp[1] = make_float4(accv[4] - cmp[4], accv[5] - cmp[5], accv[6] - cmp[6], accv[7] - cmp[7]);
@@ -686,7 +781,7 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
       const float decay = (float)cpw[sh], stp = (float)zcw[sh];
       for (int c = ct; c < nc; c += kCons * 32) {
         float S = 0.f, cS = 0.f;
-        for (int g = 0; g < L.ngrp; ++g) {
+        for (int g = 0; g < L_ngrp; ++g) {
           const float yv = part[(size_t)g * nc + c] - cS;
           const float t2 = S + yv;
           cS = (t2 - S) - yv;
@@ -720,12 +815,13 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
     if (tid == 0) {
       atomicOr(a.flag, FLAG_TIMEOUT);
       // drain this CTA's copies: each ring's last fills (bounded waits)
-      const uint32_t fulls[3] = {fullM, fullU, fullG};
-      const int nsl[3] = {L.NM, L.NU, L.NG};
-      for (int r = 0; r < 3; ++r)
-        for (int k = max(0, s_fills[r] - nsl[r]); k < s_fills[r]; ++k)
-          mbar_wait_bounded(fulls[r] + 8 * (k % nsl[r]), (uint32_t)((k / nsl[r]) & 1),
-                            kWaitBudget);
+      auto drain = [&](uint32_t full0, int nsl, int fills) {
+        for (int k = max(0, fills - nsl); k < fills; ++k)
+          mbar_wait_bounded(full0 + 8 * (k % nsl), (uint32_t)((k / nsl) & 1), kWaitBudget);
+      };
+      drain(fullM, L_NM, s_fills[0]);
+      drain(fullU, L_NU, s_fills[1]);
+      drain(fullG, L_NG, s_fills[2]);
     }
   } else {
     for (int64_t c = col0 + tid; c < min(col0 + nc, n); c += kThreads) a.x[c] = xf[c];
