@@ -419,6 +419,17 @@ typedef struct {
   int64_t wait_probe_cycles; /* as glm_ca_opts.wait_probe_cycles, for the
                          batch's tcgen05 Gram launches (glm_batch_run then
                          returns GLM_ETIMEOUT); 0 (default) = off            */
+  double tau_bound;   /* 0 (default): the Gram operand type is the one the
+                         descriptors give (else the storage type).  > 0 and
+                         no descriptor fixes it: the autotuner also chooses
+                         the batch's Gram type among FP32, TF32, FP16 and
+                         BF16 (FP32 storage; narrower storage keeps its own,
+                         already exact, type), admitting an (s, type) pair
+                         only if Theorem 1's hypothesis figure
+                         tau_G = K_s L_sigma alpha (2 u_A + gamma_G) ||H_L||
+                         (paper Sec. 5.2), bounded from one gathered outer
+                         step of up to four problems of each n, is at most
+                         tau_bound (the theorem needs <= 1/2).              */
 } glm_batch_opts;
 
 void glm_batch_opts_default(glm_batch_opts *o);
@@ -426,12 +437,14 @@ void glm_batch_opts_default(glm_batch_opts *o);
 /*
  * Upload P independent problems (each converted like glm_create_ex, with
  * per-column scales) and run the autotuner for every problem with s = 0: for
- * each n among them it times one round of s in {1, 2, 4, 8, 16} on up to 32 of those
- * problems (scratch iterates) and keeps the fastest in samples per second.
- * The tuner only chooses what leaves the exact-arithmetic iterate unchanged
- * (s; CA-SGD equals SGD for every s), never b or the operand precision.
- * Returns GLM_EINVAL on a bad descriptor (the message names the problem).
- * Blocks.
+ * each n among them it times one round of each (s, Gram kernel) -- s in
+ * {1, 2, 4, 8, 16}; the SIMT kernel or tcgen05 tiles of 128 x 128 or
+ * 128 x 256 -- on up to 32 of those problems (scratch iterates) and keeps the
+ * fastest in samples per second.  Without opts.tau_bound the tuner only
+ * chooses what leaves the exact-arithmetic iterate unchanged (s and the
+ * kernel); with it, also the Gram operand type under that accuracy bound.
+ * It never chooses b (part of the problem).  Returns GLM_EINVAL on a bad
+ * descriptor (the message names the problem).  Blocks.
  */
 int glm_batch_create(int P, const glm_problem_desc *descs,
                      const glm_batch_opts *opts, glm_batch *out);
@@ -455,6 +468,24 @@ int glm_batch_loss(glm_batch bt, float *const *xs, double *out);
 
 /* The s, b and Gram operand type used for problem p. */
 int glm_batch_choice(glm_batch bt, int p, int *s, int64_t *b, int *gram_dtype);
+
+/* The autotuner's Theorem 1 prior (paper Sec. 5.2) on host data: for the
+ * s b x n rows Y (host FP32, row-major, blocks of b rows) an upper bound on
+ * ||H_L||_2 (H_L the strictly block-lower part of |Y| |Y|^T), from
+ * sqrt(||H_L||_1 ||H_L||_inf), and the hypothesis figure
+ *   tau_G = K_s L_sigma alpha (2 u_A + gamma_G) ||H_L||_2,
+ * with K_s <= 1 / (1 - L_sigma alpha ||H_L||_2), gamma_G = 2 u_in +
+ * gamma_n(2^-24), L_sigma 1/4 (logistic) or 1 (least squares); Poisson has
+ * no Lipschitz bound (tau_G infinite unless u_in = 0).  Either output may be
+ * NULL.  Host only, no device work. */
+int glm_tau_prior(const float *Y, int64_t n, int s, int64_t b, double alpha, int loss,
+                  double u_A, double u_in, double *hl_bound, double *tau);
+
+/* The Gram kernel chosen for problem p (0 automatic, 1 SIMT, 2 tcgen05
+ * 128 x 128 tiles, 3 tcgen05 128 x 256 tiles) and the estimated tau_G at the
+ * chosen s and type (0 when not estimated: no tau_bound, or s = 1).  Host
+ * outputs, either may be NULL. */
+int glm_batch_choice_kernel(glm_batch bt, int p, int *gram_kernel, double *tau_g);
 
 int glm_batch_destroy(glm_batch bt);
 

@@ -413,6 +413,7 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
       gr.G = static_cast<float *>(h->gbuf[buf].ptr);
       gr.flag = h->dflag;
       gr.probe = p.probe;
+      gr.tile_n = 0;
       GLM_TRY(tmark(h, p, side, ci, 1, 0));
       if (p.gram_impl == 2) GLM_TRY(launch_gram_tc(gr, side));
       else if (p.gram_impl == 3) GLM_TRY(launch_gram_simt_f16acc(gr, side));
@@ -916,6 +917,7 @@ int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b, i
   a.G = G;
   a.flag = nullptr;
   a.probe = 0;
+  a.tile_n = 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (impl == 0) impl = gram_tc_supported(dtype, ld) ? 2 : 1;
   if (impl == 2) {

@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -52,13 +53,17 @@ struct Prob {
   uint64_t seed = 0;
   int s = 0;        // chosen s-step length
   int tuned = 0;    // 1: s chosen by the autotuner
+  int gk = 0;       // Gram kernel: 0 automatic, 1 SIMT, 2 tcgen05 128 x 128,
+                    // 3 tcgen05 128 x 256 (chosen with s by the autotuner)
+  double tau = 0.0; // estimated tau_G at the chosen (s, Gram type); 0 if not estimated
 };
 
-struct Group {      // problems of one round sharing (s, b, n, ld): one Gram launch
+struct Group {      // problems of one round sharing (s, b, n, Gram kernel): one Gram launch
   int s;
   int64_t b, n, ld, nouter;
   void *Y;
   float *G;
+  int gk;
 };
 
 struct Plan {
@@ -91,6 +96,8 @@ struct Batch {
   unsigned *bflag = nullptr;  // [0]: the Gram launches' flag word, [1]: the
                               // tuner's scratch runs' flag word (every item)
   int64_t probe = 0;          // glm_batch_opts.wait_probe_cycles
+  double tau_bound = 0.0;     // glm_batch_opts.tau_bound (0: Gram type not tuned)
+  bool gdt_free = false;      // no descriptor fixed the Gram type
 };
 
 namespace {
@@ -121,14 +128,14 @@ void make_plan(const Batch &B, const std::vector<int> &sel, const std::vector<in
   pl.rounds = (int)((hmax + pl.K - 1) / pl.K);
   for (int r = 0; r < pl.rounds; ++r) {
     pl.begin.push_back((int)pl.items.size());
-    // group the round's problems by (s, b, n, ld); each group is contiguous
-    std::map<std::tuple<int, int64_t, int64_t>, std::vector<std::pair<int, int64_t>>> grp;
+    // group the round's problems by (s, b, n, Gram kernel); each group is contiguous
+    std::map<std::tuple<int, int64_t, int64_t, int>, std::vector<std::pair<int, int64_t>>> grp;
     for (size_t k = 0; k < sel.size(); ++k) {
       const Prob &p = B.pr[sel[k]];
       const int64_t H = (iters[k] + p.s - 1) / p.s;
       const int64_t h0 = (int64_t)r * pl.K;
       if (h0 >= H) continue;
-      grp[std::make_tuple(p.s, p.b, p.n)].push_back({(int)k, std::min<int64_t>(pl.K, H - h0)});
+      grp[std::make_tuple(p.s, p.b, p.n, p.gk)].push_back({(int)k, std::min<int64_t>(pl.K, H - h0)});
     }
     size_t yoff = 0, loff = 0, goff = 0;
     std::vector<Group> gl;
@@ -137,7 +144,8 @@ void make_plan(const Batch &B, const std::vector<int> &sel, const std::vector<in
       const int s = std::get<0>(kv.first);
       const int64_t b = std::get<1>(kv.first), n = std::get<2>(kv.first);
       const int64_t sb = s * b, ld = ld_for(n);
-      Group g{s, b, n, ld, 0, reinterpret_cast<void *>(yoff), reinterpret_cast<float *>(goff)};
+      Group g{s, b, n, ld, 0, reinterpret_cast<void *>(yoff), reinterpret_cast<float *>(goff),
+              std::get<3>(kv.first)};
       for (auto &e : kv.second) {
         const int k = e.first;
         const int64_t nout = e.second;
@@ -247,7 +255,9 @@ int enqueue(Batch &B, const Plan &pl, cudaStream_t st) {
       ga.G = reinterpret_cast<float *>(gb + reinterpret_cast<size_t>(g.G));
       ga.flag = B.bflag;
       ga.probe = B.probe;
-      const bool tc = B.gram_impl == 2 || (B.gram_impl == 0 && gram_tc_supported(B.gdt, g.ld));
+      const bool tc_ok = gram_tc_supported(B.gdt, g.ld);
+      const bool tc = g.gk >= 2 ? tc_ok : (g.gk == 0 && tc_ok);
+      ga.tile_n = g.gk == 2 ? 128 : (g.gk == 3 ? 256 : 0);
       if (tc) GLM_TRY(launch_gram_tc(ga, st));
       else GLM_TRY(launch_gram_simt(ga, st));
     }
@@ -258,9 +268,9 @@ int enqueue(Batch &B, const Plan &pl, cudaStream_t st) {
 }
 
 // Time one round of candidate s for the problems `sel` (scratch iterates).
-int time_candidate(Batch &B, const std::vector<int> &sel, int s, float *xscratch, double &ms,
-                   double &samples) {
-  std::vector<int> keep(sel.size());
+int time_candidate(Batch &B, const std::vector<int> &sel, int s, int gk, float *xscratch,
+                   double &ms, double &samples) {
+  std::vector<int> keep(sel.size()), keepk(sel.size());
   std::vector<int64_t> iters(sel.size());
   std::vector<float *> xp(sel.size());
   std::vector<int> kmap(B.P, -1);
@@ -269,7 +279,9 @@ int time_candidate(Batch &B, const std::vector<int> &sel, int s, float *xscratch
   for (size_t k = 0; k < sel.size(); ++k) {
     Prob &p = B.pr[sel[k]];
     keep[k] = p.s;
+    keepk[k] = p.gk;
     p.s = s;
+    p.gk = gk;
     iters[k] = std::min<int64_t>(p.iters, (int64_t)8 * s);  // eight outer steps
     samples += (double)iters[k] * (double)p.b;
     xp[k] = xscratch + xo;
@@ -300,10 +312,121 @@ int time_candidate(Batch &B, const std::vector<int> &sel, int s, float *xscratch
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  for (size_t k = 0; k < sel.size(); ++k) B.pr[sel[k]].s = keep[k];
+  for (size_t k = 0; k < sel.size(); ++k) {
+    B.pr[sel[k]].s = keep[k];
+    B.pr[sel[k]].gk = keepk[k];
+  }
   return rc;
 }
 
+// ---- Theorem 1 prior (paper Sec. 5.2) for the Gram operand type ----------
+// tau_G = K_s L_sigma alpha (2 u_A + gamma_G) ||H_L||_2 is the theorem's
+// hypothesis figure for the Gram slot: the local budget holds for tau_G <=
+// 1/2, and it scales the Gram term E_G.  From one gathered outer step of a
+// problem (FP32 values of its stored rows) the tuner bounds
+//   ||H_L||_2 <= sqrt(||H_L||_1 ||H_L||_inf),  H_L = strictly block-lower |Y||Y|^T,
+// both norms from prefix sums of |rows| over blocks (O(s b n)), and
+//   K_s = ||(I - L alpha |G_L|)^-1||_2 <= 1 / (1 - L alpha ||H_L||_2).
+double hl_norm_bound(const std::vector<float> &Y, int64_t n, int s, int64_t b) {
+  std::vector<double> pre(n, 0.0), suf(n, 0.0), absr(n);
+  double ninf = 0.0, none = 0.0;
+  // infinity norm: row r of block j against the sum of |rows| of blocks < j
+  for (int j = 0; j < s; ++j) {
+    for (int64_t l = 0; l < b; ++l) {
+      const float *y = Y.data() + ((int64_t)j * b + l) * n;
+      double acc = 0.0;
+      for (int64_t c = 0; c < n; ++c) acc += std::fabs((double)y[c]) * pre[c];
+      ninf = std::max(ninf, acc);
+    }
+    for (int64_t l = 0; l < b; ++l) {
+      const float *y = Y.data() + ((int64_t)j * b + l) * n;
+      for (int64_t c = 0; c < n; ++c) pre[c] += std::fabs((double)y[c]);
+    }
+  }
+  // one norm: column (row of Y) c of block i against |rows| of blocks > i
+  for (int i = s - 1; i >= 0; --i) {
+    for (int64_t l = 0; l < b; ++l) {
+      const float *y = Y.data() + ((int64_t)i * b + l) * n;
+      double acc = 0.0;
+      for (int64_t c = 0; c < n; ++c) acc += std::fabs((double)y[c]) * suf[c];
+      none = std::max(none, acc);
+    }
+    for (int64_t l = 0; l < b; ++l) {
+      const float *y = Y.data() + ((int64_t)i * b + l) * n;
+      for (int64_t c = 0; c < n; ++c) suf[c] += std::fabs((double)y[c]);
+    }
+  }
+  return std::sqrt(ninf * none);
+}
+
+double unit_roundoff(int dt) {
+  switch (dt) {
+  case GLM_BF16: return std::ldexp(1.0, -8);
+  case GLM_F16: case GLM_TF32: return std::ldexp(1.0, -11);
+  }
+  return 0.0;  // FP32 storage values are the data
+}
+
+// Rounding of stored values to Gram operands of type `gdt`: none when every
+// stored value is representable (FP32 operands; TF32 holds BF16 and FP16).
+double operand_roundoff(int gdt, int storage) {
+  if (gdt == storage || gdt == GLM_F32) return 0.0;
+  if (gdt == GLM_TF32 && (storage == GLM_BF16 || storage == GLM_F16)) return 0.0;
+  return unit_roundoff(gdt);
+}
+
+double tau_g(double hl, double alpha, int loss, double u_A, double u_in, int64_t n) {
+  if (loss == GLM_POISSON) return u_in > 0.0 ? INFINITY : 0.0;  // no Lipschitz bound
+  const double L = loss == GLM_LOGISTIC ? 0.25 : 1.0;
+  const double q = (double)n * std::ldexp(1.0, -24);
+  const double gamma_G = 2.0 * u_in + q / (1.0 - q);
+  const double a = L * alpha * hl;
+  if (a >= 1.0) return INFINITY;
+  return (1.0 / (1.0 - a)) * L * alpha * (2.0 * u_A + gamma_G) * hl;
+}
+
+// FP32 values of the stored rows of problem p's first outer step of `rows`
+// rows (its own index stream), on the host.
+int sample_rows(Batch &B, int p, int64_t rows, std::vector<float> &out) {
+  const Handle *h = reinterpret_cast<const Handle *>(B.pr[p].h);
+  const int64_t ld = round_up(h->n, 8);
+  float *d = nullptr, *lab = nullptr;
+  GLM_CUDA_TRY(dev_malloc((void **)&d, (size_t)rows * ld * 4));
+  if (dev_malloc((void **)&lab, (size_t)round_up(rows, 4) * 4) != cudaSuccess) {
+    cudaFree(d);
+    return set_error(GLM_ENOMEM, "autotune: sample buffer");
+  }
+  GatherArgs ga;
+  memset(&ga, 0, sizeof(ga));
+  ga.A = h->A; ga.lda = h->lda; ga.a_dt = h->dtype; ga.colscale = h->colscale;
+  ga.y = h->y; ga.m = h->m; ga.n = h->n; ga.rows = rows;
+  ga.q0 = 0; ga.seed = B.pr[p].seed; ga.problem = (uint64_t)p;
+  ga.out1 = d; ga.dt1 = GLM_F32; ga.ld1 = ld;
+  ga.ylab = lab; ga.lab_sb = rows; ga.lab_sbp = round_up(rows, 4);
+  int rc = launch_gather(ga, B.stream);
+  std::vector<float> tmp((size_t)rows * ld);
+  if (rc == GLM_OK && cudaMemcpyAsync(tmp.data(), d, tmp.size() * 4, cudaMemcpyDeviceToHost,
+                                      B.stream) != cudaSuccess)
+    rc = set_error(GLM_ECUDA, "autotune: sample copy");
+  if (rc == GLM_OK && cudaStreamSynchronize(B.stream) != cudaSuccess)
+    rc = set_error(GLM_ECUDA, "autotune: sample sync");
+  cudaFree(d);
+  cudaFree(lab);
+  if (rc != GLM_OK) return rc;
+  out.resize((size_t)rows * h->n);
+  for (int64_t r = 0; r < rows; ++r)
+    memcpy(out.data() + r * h->n, tmp.data() + r * ld, (size_t)h->n * 4);
+  return GLM_OK;
+}
+
+// The autotuner.  For every n among the problems left to it (up to 32 of
+// them timed, up to 4 sampled for the prior) and, under a caller bound on
+// tau_G, for every admissible Gram operand type of the batch, it times one
+// round of each candidate (s, Gram kernel) -- s in {1, 2, 4, 8, 16}; SIMT,
+// tcgen05 128 x 128 or 128 x 256 tiles -- and keeps the fastest in samples
+// per second.  With a bound, (s, type) pairs whose estimated tau_G exceeds it
+// are not timed (s = 1 has no Gram and is always admissible), and the type
+// kept is the one with the shortest estimated run over all problems.
 int autotune(Batch &B) {
   std::map<int64_t, std::vector<int>> by_n;  // problems left to the tuner, by n
   for (int p = 0; p < B.P; ++p)
@@ -314,25 +437,97 @@ int autotune(Batch &B) {
   for (auto &kv : by_n) xcount = std::max(xcount, std::min<size_t>(kv.second.size(), 32) *
                                                       (size_t)round_up(kv.first, 8));
   GLM_CUDA_TRY(dev_malloc((void **)&xs, xcount * 4));
+  const int svals[5] = {1, 2, 4, 8, 16};
+  // ||H_L|| bounds per (problem sampled, s): prefixes of one 16-step sample
+  std::map<int, std::vector<double>> hl;  // problem -> bound for each s value
   int rc = GLM_OK;
-  for (auto &kv : by_n) {
-    std::vector<int> sel(kv.second.begin(),
-                         kv.second.begin() + std::min<size_t>(kv.second.size(), 32));
-    int best = 8;
-    double best_rate = -1.0;
-    for (int s : {1, 2, 4, 8, 16}) {
-      if (cudaMemsetAsync(xs, 0, xcount * 4, B.stream) != cudaSuccess) {
-        rc = set_error(GLM_ECUDA, "autotune: cudaMemsetAsync");
-        break;
+  if (B.tau_bound > 0.0) {
+    for (auto &kv : by_n) {
+      for (size_t k = 0; k < kv.second.size() && k < 4 && rc == GLM_OK; ++k) {
+        const int p = kv.second[k];
+        // up to 16 outer-step blocks (64 M values at most): longer s is not admitted
+        const int steps = (int)std::max<int64_t>(
+            1, std::min<int64_t>(16, (64ll << 20) / (B.pr[p].b * B.pr[p].n)));
+        std::vector<float> Y;
+        rc = sample_rows(B, p, (int64_t)steps * B.pr[p].b, Y);
+        if (rc != GLM_OK) break;
+        std::vector<double> v;
+        for (int si : svals)
+          v.push_back(si <= steps ? hl_norm_bound(Y, B.pr[p].n, si, B.pr[p].b) : INFINITY);
+        hl[p] = v;
       }
-      double ms = 0.0, samples = 0.0;
-      rc = time_candidate(B, sel, s, xs, ms, samples);
-      if (rc != GLM_OK) break;
-      const double rate = samples / std::max(ms, 1e-6);
-      if (rate > best_rate) { best_rate = rate; best = s; }
     }
+  }
+  std::vector<int> types = {B.gdt};
+  if (B.tau_bound > 0.0 && B.gdt_free) {
+    if (B.dtype == GLM_F32) types = {GLM_F32, GLM_TF32, GLM_F16, GLM_BF16};
+    else types = {B.dtype};  // narrower storage: its own type is exact and fastest
+  }
+  struct Choice { int s = 1, gk = 0; double rate = -1.0; };
+  double best_total = INFINITY;
+  int best_type = B.gdt;
+  std::map<int64_t, Choice> best_choice;
+  for (int T : types) {
     if (rc != GLM_OK) break;
-    for (int p : kv.second) B.pr[p].s = best;
+    B.gdt = T;
+    const double u_in = operand_roundoff(T, B.dtype), u_A = unit_roundoff(B.dtype);
+    std::map<int64_t, Choice> ch;
+    double total = 0.0;
+    for (auto &kv : by_n) {
+      std::vector<int> sel(kv.second.begin(),
+                           kv.second.begin() + std::min<size_t>(kv.second.size(), 32));
+      const bool tc_ok = gram_tc_supported(T, round_up(kv.first, 64));
+      Choice c;
+      for (int si = 0; si < 5 && rc == GLM_OK; ++si) {
+        const int sv = svals[si];
+        if (B.tau_bound > 0.0 && sv > 1) {  // the prior: every sampled problem admits it
+          double tmax = 0.0;
+          for (size_t k = 0; k < kv.second.size() && k < 4; ++k) {
+            const Prob &q = B.pr[kv.second[k]];
+            tmax = std::max(tmax, tau_g(hl[kv.second[k]][si], (double)q.eta / (double)q.b,
+                                        q.loss, u_A, u_in, q.n));
+          }
+          if (!(tmax <= B.tau_bound)) continue;
+        }
+        std::vector<int> kernels = {0};
+        if (sv > 1) kernels = tc_ok ? std::vector<int>{1, 2, 3} : std::vector<int>{1};
+        for (int gk : kernels) {
+          if (cudaMemsetAsync(xs, 0, xcount * 4, B.stream) != cudaSuccess) {
+            rc = set_error(GLM_ECUDA, "autotune: cudaMemsetAsync");
+            break;
+          }
+          double ms = 0.0, samples = 0.0;
+          rc = time_candidate(B, sel, sv, gk, xs, ms, samples);
+          if (rc != GLM_OK) break;
+          const double rate = samples / std::max(ms, 1e-6);
+          if (rate > c.rate) { c.rate = rate; c.s = sv; c.gk = gk; }
+        }
+      }
+      ch[kv.first] = c;
+      double work = 0.0;  // samples of all this n's problems at the chosen rate
+      for (int p : kv.second) work += (double)B.pr[p].iters * (double)B.pr[p].b;
+      total += work / std::max(c.rate, 1e-12);
+    }
+    if (rc == GLM_OK && total < best_total) {
+      best_total = total;
+      best_type = T;
+      best_choice = ch;
+    }
+  }
+  if (rc == GLM_OK) {
+    B.gdt = best_type;
+    for (auto &kv : by_n)
+      for (int p : kv.second) {
+        B.pr[p].s = best_choice[kv.first].s;
+        B.pr[p].gk = best_choice[kv.first].gk;
+        const int si = (int)(std::find(svals, svals + 5, B.pr[p].s) - svals);
+        auto it = hl.find(kv.second[0]);
+        B.pr[p].tau = (it != hl.end() && B.pr[p].s > 1)
+                          ? tau_g(it->second[si], (double)B.pr[p].eta / (double)B.pr[p].b,
+                                  B.pr[p].loss, unit_roundoff(B.dtype),
+                                  operand_roundoff(B.gdt, B.dtype), B.pr[p].n)
+                          : 0.0;
+      }
   }
   // the scratch runs' flags (a diverging candidate, a timed-out Gram) say
   // nothing about the problems' own runs: clear both words
@@ -361,6 +556,7 @@ void glm_batch_opts_default(glm_batch_opts *o) {
   o->input_on_host = 1;
   o->stream = nullptr;
   o->wait_probe_cycles = 0;
+  o->tau_bound = 0.0;
 }
 
 int glm_batch_destroy(glm_batch bt) {
@@ -390,6 +586,7 @@ int glm_batch_create(int P, const glm_problem_desc *descs, const glm_batch_opts 
   if (opts->dtype != GLM_F32 && opts->dtype != GLM_BF16 && opts->dtype != GLM_F16)
     return set_error(GLM_EINVAL, "batch storage dtype must be F32, BF16 or F16");
   if (opts->wait_probe_cycles < 0) return set_error(GLM_EINVAL, "wait_probe_cycles must be >= 0");
+  if (!(opts->tau_bound >= 0.0)) return set_error(GLM_EINVAL, "tau_bound must be >= 0");
   int gdt = -1;
   for (int p = 0; p < P; ++p) {
     const glm_problem_desc &d = descs[p];
@@ -432,6 +629,8 @@ int glm_batch_create(int P, const glm_problem_desc *descs, const glm_batch_opts 
     B->own_stream = true;
   }
   B->probe = opts->wait_probe_cycles;
+  B->tau_bound = opts->tau_bound;
+  B->gdt_free = gdt < 0;
   if (dev_malloc((void **)&B->bflag, 4 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemsetAsync(B->bflag, 0, 4 * sizeof(unsigned), B->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -551,6 +750,28 @@ int glm_batch_loss(glm_batch bt, float *const *xs, double *out) {
     if (!xs[p]) return set_error(GLM_EINVAL, "iterate pointer of a problem is NULL");
     GLM_TRY(glm_loss(B->pr[p].h, xs[p], B->pr[p].lambda, &out[p]));
   }
+  return GLM_OK;
+}
+
+int glm_tau_prior(const float *Y, int64_t n, int s, int64_t b, double alpha, int loss,
+                  double u_A, double u_in, double *hl_bound, double *tau) {
+  set_error(GLM_OK, "");
+  if (!Y || n < 1 || s < 1 || b < 1) return set_error(GLM_EINVAL, "bad arguments");
+  if (loss != GLM_LOGISTIC && loss != GLM_LSQ && loss != GLM_POISSON)
+    return set_error(GLM_EINVAL, "bad loss");
+  std::vector<float> v(Y, Y + (size_t)s * b * n);
+  const double hl = hl_norm_bound(v, n, s, b);
+  if (hl_bound) *hl_bound = hl;
+  if (tau) *tau = tau_g(hl, alpha, loss, u_A, u_in, n);
+  return GLM_OK;
+}
+
+int glm_batch_choice_kernel(glm_batch bt, int p, int *gram_kernel, double *tau_g) {
+  set_error(GLM_OK, "");
+  Batch *B = reinterpret_cast<Batch *>(bt);
+  if (!B || p < 0 || p >= B->P) return set_error(GLM_EINVAL, "bad batch or problem index");
+  if (gram_kernel) *gram_kernel = B->pr[p].gk;
+  if (tau_g) *tau_g = B->pr[p].tau;
   return GLM_OK;
 }
 

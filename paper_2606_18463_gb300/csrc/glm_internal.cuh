@@ -438,6 +438,7 @@ struct GramArgs {
   float *G;
   unsigned *flag;         // device flag word for FLAG_TIMEOUT, or null
   long long probe;        // > 0: failure-path probe wait (SM cycles), else 0
+  int tile_n;             // tcgen05 tile width: 0 automatic, 128 or 256
 };
 int launch_gram_simt(const GramArgs &a, cudaStream_t st);
 int launch_gram_tc(const GramArgs &a, cudaStream_t st);

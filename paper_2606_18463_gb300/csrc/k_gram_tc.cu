@@ -424,9 +424,11 @@ int launch_gram_tc_impl(const GramArgs &g, cudaStream_t st, bool acc16) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // wide tiles unless they would leave SMs idle (few, long-K tiles)
+  // wide tiles unless they would leave SMs idle (few, long-K tiles), or as
+  // the caller asks (the batched autotuner times both)
   const int64_t wide = g.nouter * tiles_per_outer<256>(sb);
-  if (wide >= sms) return launch_n<256>(a, sms, wide, st, acc16);
+  if (g.tile_n == 256 || (g.tile_n == 0 && wide >= sms))
+    return launch_n<256>(a, sms, wide, st, acc16);
   return launch_n<128>(a, sms, g.nouter * tiles_per_outer<128>(sb), st, acc16);
 }
 

@@ -40,7 +40,7 @@ EXPORTED = [
     "glm_storage_layout", "glm_storage_read", "glm_debug_fail_alloc",
     "glm_slab_reduce_floats", "glm_slab_partial", "glm_slab_finish", "glm_sum_buffers",
     "glm_batch_opts_default", "glm_batch_create", "glm_batch_run", "glm_batch_loss",
-    "glm_batch_choice", "glm_batch_destroy",
+    "glm_batch_choice", "glm_batch_choice_kernel", "glm_tau_prior", "glm_batch_destroy",
 ]
 
 
@@ -85,7 +85,7 @@ class glm_problem_desc(ctypes.Structure):
 class glm_batch_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("input_dtype", ctypes.c_int),
                 ("input_on_host", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("wait_probe_cycles", ctypes.c_int64)]
+                ("wait_probe_cycles", ctypes.c_int64), ("tau_bound", ctypes.c_double)]
 
 
 _lib = None
@@ -148,6 +148,11 @@ def load():
             "glm_batch_loss": ([vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)], i32),
             "glm_batch_choice": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                   ctypes.POINTER(i32)], i32),
+            "glm_batch_choice_kernel": ([vp, i32, ctypes.POINTER(i32),
+                                         ctypes.POINTER(ctypes.c_double)], i32),
+            "glm_tau_prior": ([vp, i64, i32, i64, ctypes.c_double, i32, ctypes.c_double,
+                               ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)], i32),
             "glm_batch_destroy": ([vp], i32),
         }
         for name, (args, res) in sig.items():
@@ -437,6 +442,22 @@ def glm_batch_choice(bt, p):
     return s.value, b.value, g.value
 
 
+def glm_batch_choice_kernel(bt, p):
+    k, t = ctypes.c_int(), ctypes.c_double()
+    _check(load().glm_batch_choice_kernel(bt, p, ctypes.byref(k), ctypes.byref(t)))
+    return k.value, t.value
+
+
+def glm_tau_prior(Y, s, b, alpha, loss, u_A, u_in):
+    """(||H_L||_2 bound, tau_G) of the autotuner's prior for host rows Y."""
+    import numpy as np
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    hl, tau = ctypes.c_double(), ctypes.c_double()
+    _check(load().glm_tau_prior(Y.ctypes.data, Y.shape[1], s, b, alpha, loss, u_A, u_in,
+                                ctypes.byref(hl), ctypes.byref(tau)))
+    return hl.value, tau.value
+
+
 def glm_batch_destroy(bt):
     _check(load().glm_batch_destroy(bt))
 
@@ -446,7 +467,8 @@ class Batch:
     A (host numpy (m, n) float32), y, loss, lam, eta, iters, seed, b and
     optionally s (0 = autotuned) and gram ('f32', 'tf32', 'bf16', 'f16')."""
 
-    def __init__(self, problems, dtype="bf16", stream=None, wait_probe_cycles=0):
+    def __init__(self, problems, dtype="bf16", stream=None, wait_probe_cycles=0,
+                 tau_bound=0.0):
         import numpy as np
         import torch
         self._keep = []
@@ -471,6 +493,7 @@ class Batch:
         st = stream if stream is not None else torch.cuda.current_stream()
         o.stream = st.cuda_stream or 1
         o.wait_probe_cycles = wait_probe_cycles
+        o.tau_bound = tau_bound
         self.stream = st
         self.P = len(descs)
         self.h = glm_batch_create(self.P, descs, o)
@@ -484,6 +507,9 @@ class Batch:
 
     def choice(self, p):
         return glm_batch_choice(self.h, p)
+
+    def choice_kernel(self, p):
+        return glm_batch_choice_kernel(self.h, p)
 
     def close(self):
         if getattr(self, "h", None):

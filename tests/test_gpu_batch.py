@@ -143,3 +143,63 @@ def test_batch_argument_errors(G):
     with pytest.raises(G.GlmError) as e:
         G.Batch(probs, dtype="f32")
     assert e.value.code == G.GLM_EINVAL
+
+
+def test_batch_tuner_gram_kernel_and_tile(G):
+    # BF16 storage: the tuner times the SIMT kernel and both tcgen05 tiles for
+    # every s > 1 and reports its choice; results are held to the final-loss bar
+    probs = _make([(3000, 64, oracle.LOGISTIC, 1e-4, 0), (2500, 128, oracle.LSQ, 1e-3, 0),
+                   (2000, 256, oracle.LOGISTIC, 1e-3, 0), (1800, 512, oracle.LSQ, 1e-3, 0)],
+                  seed0=30)
+    bt = G.Batch(probs, dtype="bf16")
+    try:
+        for k in range(len(probs)):
+            s, _, _ = bt.choice(k)
+            gk, tau = bt.choice_kernel(k)
+            assert (s == 1 and gk == 0) or (s > 1 and gk in (1, 2, 3)), (s, gk)
+            assert tau == 0.0                   # no bound asked: not estimated
+        xs = _zeros(probs)
+        assert bt.run(xs) == [G.GLM_OK] * len(probs)
+        for k, p in enumerate(probs):
+            ref = oracle.sgd(p["A"], p["y"], p["loss"], B, ETA, p["lam"], ITERS, p["seed"],
+                             problem=k)
+            f = oracle.loss(p["A"], p["y"], p["loss"], p["lam"], xs[k].cpu().numpy())
+            fr = oracle.loss(p["A"], p["y"], p["loss"], p["lam"], ref)
+            assert abs(f - fr) <= 1e-3 * fr, (k, f, fr)
+    finally:
+        bt.close()
+
+
+@pytest.mark.parametrize("bound", [0.5, 1e-12])
+def test_batch_tuner_theorem_prior(G, bound):
+    # FP32 storage with a bound on tau_G: the tuner may pick a narrower Gram
+    # type only where the prior admits it.  Every problem's estimated tau_G at
+    # its (s, type) stays within the bound (s = 1 needs no Gram); with an
+    # impossible bound every problem runs plain SGD and matches the oracle
+    # at 1e-5.
+    probs = _make([(3000, 64, oracle.LOGISTIC, 1e-4, 0), (2500, 128, oracle.LSQ, 1e-3, 0),
+                   (2000, 256, oracle.LOGISTIC, 1e-3, 0)], seed0=40)
+    bt = G.Batch(probs, dtype="f32", tau_bound=bound)
+    try:
+        gdt = bt.choice(0)[2]
+        assert gdt in (G.GLM_F32, G.GLM_TF32, G.GLM_F16, G.GLM_BF16)
+        for k in range(len(probs)):
+            s, _, g2 = bt.choice(k)
+            gk, tau = bt.choice_kernel(k)
+            assert g2 == gdt
+            assert tau <= bound, (k, s, tau)
+            if bound < 1e-9:
+                assert s == 1
+        xs = _zeros(probs)
+        assert bt.run(xs) == [G.GLM_OK] * len(probs)
+        for k, p in enumerate(probs):
+            ref = oracle.sgd(p["A"], p["y"], p["loss"], B, ETA, p["lam"], ITERS, p["seed"],
+                             problem=k)
+            got = xs[k].cpu().numpy().astype(np.float64)
+            if bound < 1e-9:
+                assert _rel(got, ref) <= 1e-5
+            f = oracle.loss(p["A"], p["y"], p["loss"], p["lam"], got)
+            fr = oracle.loss(p["A"], p["y"], p["loss"], p["lam"], ref)
+            assert abs(f - fr) <= 1e-3 * fr
+    finally:
+        bt.close()
