@@ -151,6 +151,21 @@ typedef struct {
                          else GLM_EINVAL; never chosen automatically).       */
   int timing;         /* 1: record CUDA events around every kernel of the run
                          (read back with glm_kernel_times).  Default 0.       */
+  int accumulate;     /* GLM_F32 (default) or GLM_F16: FP16 accumulation in
+                         the margin and gradient GEMVs (Recipe F's h_a slots;
+                         FP16 GEMV operands required; pair it with gram_impl
+                         3 or 4 for the FP16-accumulate Gram).               */
+  int state_dtype;    /* GLM_F32 (default), GLM_BF16 (Recipe I) or GLM_F16
+                         (Recipe H): CA-SGD end to end in that type -- the
+                         margins, the Gram output, each correction, residual
+                         and history entry, the gradient and the weights are
+                         rounded to it once each (x is rounded on entry and
+                         holds values of the type on return); Gram and GEMV
+                         operands must be that type; the correction sums
+                         accumulate in FP16 when accumulate is GLM_F16.
+                         Either field away from GLM_F32 runs a per-step
+                         numerical baseline (one kernel per stage and outer
+                         iteration, no graph), not the fused chain.          */
   int chain_impl;     /* x-dependent chain kernel: 0 (default) automatic, 1
                          resident (the step's Y and G staged whole in the
                          cluster's shared memory), 2 streaming (Y and G

@@ -540,6 +540,8 @@ void glm_ca_opts_default(glm_ca_opts *o) {
   o->chunk_outer = 0;
   o->gram_impl = 0;
   o->timing = 0;
+  o->accumulate = GLM_F32;
+  o->state_dtype = GLM_F32;
   o->chain_impl = 0;
   o->wait_probe_cycles = 0;
 }
@@ -725,6 +727,11 @@ int glm_sgd_run(glm_handle h, int64_t b, float eta, float lambda, int64_t iters,
 int glm_ca_sgd_run_ex(glm_handle hh, int s, int64_t b, float eta, float lambda, int64_t iters,
                       uint64_t seed, float *x, const glm_ca_opts *opts) {
   g_last_error.clear();
+  if (opts && (opts->accumulate != GLM_F32 || opts->state_dtype != GLM_F32)) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return set_error(GLM_EINVAL, "null handle");
+    return run_recipe(h, s, b, eta, lambda, iters, seed, x, opts);
+  }
   return run_common(reinterpret_cast<Handle *>(hh), s, b, eta, lambda, iters, seed, x, opts,
                     false);
 }

@@ -500,6 +500,9 @@ int launch_chain_batch(const BatchItem *items, const int *order, int nitems, int
                        int y_dt, int rec64, int max_n, int max_sb, int max_s, cudaStream_t st);
 
 int launch_loss(Handle *h, const float *x, float lambda, cudaStream_t st);
+// CA-SGD under a narrow precision recipe (glm_ca_opts.accumulate / state_dtype)
+int run_recipe(Handle *h, int s, int64_t b, float eta, float lambda, int64_t iters,
+               uint64_t seed, float *x, const glm_ca_opts *o);
 int launch_sample(uint64_t seed, uint64_t problem, int64_t first, int64_t count,
                   int64_t m, int32_t *out, cudaStream_t st);
 int launch_create_convert(Handle *h, const void *src, int src_dt, int64_t row0,

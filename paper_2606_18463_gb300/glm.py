@@ -62,7 +62,8 @@ class glm_ca_opts(ctypes.Structure):
                 ("first_iter", ctypes.c_int64), ("problem", ctypes.c_uint32),
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("chunk_outer", ctypes.c_int64), ("gram_impl", ctypes.c_int),
-                ("timing", ctypes.c_int), ("chain_impl", ctypes.c_int),
+                ("timing", ctypes.c_int), ("accumulate", ctypes.c_int),
+                ("state_dtype", ctypes.c_int), ("chain_impl", ctypes.c_int),
                 ("wait_probe_cycles", ctypes.c_int64)]
 
 
@@ -196,7 +197,7 @@ def default_ca_opts(**kw) -> glm_ca_opts:
     o = glm_ca_opts()
     load().glm_ca_opts_default(ctypes.byref(o))
     for k, v in kw.items():
-        if k in ("gram_dtype", "gemv_dtype") and isinstance(v, str):
+        if k in ("gram_dtype", "gemv_dtype", "accumulate", "state_dtype") and isinstance(v, str):
             v = DTYPES[v]
         setattr(o, k, v)
     return o

@@ -1,0 +1,241 @@
+"""CA-SGD under the narrow precision recipes of Sec. 5.3 that the fused chain
+does not carry (glm_ca_opts.accumulate and .state_dtype), through the C ABI:
+
+  F  FP16 accumulation in the margin and gradient GEMVs (FP16 operands), FP32
+     state; with the FP16-accumulate Gram (gram_impl 3 or 4) or FP32
+     accumulation in the Gram;
+  H  end-to-end FP16: margins, Gram output, corrections, residuals, history,
+     gradient and weights rounded to FP16 once each, FP16 accumulation in the
+     GEMVs and the correction sums (FP32 accumulation variant too);
+  I  end-to-end BF16 with FP32 accumulation.
+
+Parity: one outer step from a mid-training iterate stays within twice
+Theorem 1's first-order budget (Sec. 5.2) of the exact FP64 outer step over
+the same rows, with the slots of these kernels' rounding points (T the state
+type, u_T its unit roundoff, u_in the operand rounding, FP32 storage):
+  gamma_r  2 u_in + gamma_n(u_acc), plus u_T for the margin's rounding to T;
+  gamma_G  2 u_in + gamma_n(u_acc of the Gram), plus u_T for G read in T;
+  u_c      u_T + 2^-23 (the FP32 combination, then its rounding to T; FP32
+           state: 2^-24);
+  u_sigma  u_T with C_delta = 1 + u_T + C32 2^-24 / u_T, C32 the FP32
+           evaluation's constant of the fused path's budget (logistic
+           10 + 2.35 M, least squares 2); FP32 state: 2^-24 with C32;
+  gamma_g  2 u_in + gamma_{sb}(u_acc), plus u_T for the gradient's rounding;
+  u_x      u_T + 2^-23 (one FP32 fused multiply-add, then the rounding to T;
+           FP32 state: 2^-24).
+Least squares with an FP16-accumulate Gram lies outside the theorem at this
+shape (tau_G > 1/2, as for the fused path), and is held to a finite result
+and the failed hypothesis instead.
+
+Accuracy (the end-to-end check of Sec. 7, "Accuracy gap"): final-loss gap to
+FP32 CA-SGD (the fused path) over three seeds at (m, n) = (65,536, 4,096),
+b = 32, s = 16, 3,200 iterations, against the paper's 0.5 % threshold.  As
+for the mini-batch baselines, BF16 weights stall on least squares and
+Poisson (one step's update is under half a BF16 ulp of the weight); those
+cells are held to the stall's signature: the loss lies between the FP32
+run's and the starting loss.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import local_error as le
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+U32 = 2.0 ** -24
+U_OP = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+U_ST = {"f32": 0.0, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2606_18463_gb300 import glm
+    glm.load()
+    return glm
+
+
+def _round_t(v, st):
+    v = np.asarray(v, dtype=np.float32)
+    if st == "bf16":
+        return oracle.round_bf16(v)
+    if st == "f16":
+        return v.astype(np.float16).astype(np.float32)
+    return v
+
+
+# ----------------------------------------------------------------------------
+# Arguments
+# ----------------------------------------------------------------------------
+def test_recipe_arguments(G):
+    rng = np.random.default_rng(0)
+    A = torch.from_numpy((rng.standard_normal((512, 64)) / 8).astype(np.float32)).cuda()
+    y = torch.from_numpy(np.where(rng.random(512) < 0.5, -1.0, 1.0).astype(np.float32)).cuda()
+    x = torch.zeros(64, dtype=torch.float32, device="cuda")
+    d = G.Dataset(A, y, G.GLM_LOGISTIC, "f32")
+    bad = [dict(accumulate="f16", gram_dtype="f32"),            # FP16 sums, FP32 operands
+           dict(accumulate="bf16", gram_dtype="bf16"),          # no BF16 accumulation
+           dict(accumulate=7, gram_dtype="f16"),
+           dict(state_dtype="bf16", gram_dtype="f32"),          # state needs T operands
+           dict(state_dtype="f16", gram_dtype="f16", gemv_dtype="bf16"),
+           dict(state_dtype="bf16", accumulate="f16", gram_dtype="bf16", gemv_dtype="f16"),
+           dict(state_dtype="e4m3", gram_dtype="f16"),
+           dict(state_dtype="f16", gram_dtype="f16", recurrence_f64=1)]
+    try:
+        for kw in bad:
+            with pytest.raises(G.GlmError) as e:
+                d.ca_sgd(x, 4, 16, 0.5, 0.0, 8, 0, **kw)
+            assert e.value.code == G.GLM_EINVAL, kw
+        with pytest.raises(G.GlmError) as e:  # s b above the one-CTA recurrence's 8,192
+            d.ca_sgd(x, 64, 256, 0.5, 0.0, 64, 0, state_dtype="f16", gram_dtype="f16")
+        assert e.value.code == G.GLM_EINVAL
+        # zero iterations leave x untouched, not even rounded to the state type
+        x.fill_(0.1)
+        d.ca_sgd(x, 4, 16, 0.5, 0.0, 0, 0, state_dtype="f16", gram_dtype="f16")
+        d.sync()
+        assert torch.all(x == 0.1)
+    finally:
+        d.close()
+
+
+# ----------------------------------------------------------------------------
+# One outer step against Theorem 1
+# ----------------------------------------------------------------------------
+M1, N1, B1, S1, ETA1, K0, SEED = 65536, 512, 64, 8, 0.5, 4096, 5
+
+# (name, accumulate, state, Gram operand type, GEMV operand type, Gram impl)
+STEP_MODES = [
+    pytest.param("F", "f16", "f32", "f16", "f16", 0, id="F-gram32acc"),
+    pytest.param("F", "f16", "f32", "f16", "f16", 4, id="F-gram16acc-tc"),
+    pytest.param("F", "f16", "f32", "bf16", "f16", 0, id="F-bf16gram"),
+    pytest.param("H", "f16", "f16", "f16", "f16", 0, id="H-gram32acc"),
+    pytest.param("H", "f16", "f16", "f16", "f16", 3, id="H-gram16acc"),
+    pytest.param("H", "f32", "f16", "f16", "f16", 0, id="H-acc32"),
+    pytest.param("I", "f32", "bf16", "bf16", "bf16", 0, id="I"),
+]
+
+
+@pytest.fixture(scope="module", params=["logistic", "lsq"])
+def step_case(request, G):
+    if request.param == "logistic":
+        pr = synth.logistic_planted(M1, N1, seed=21, flip=0.05)
+    else:
+        pr = synth.lsq_planted(M1, N1, seed=22, noise=0.1)
+    A = pr.A.astype(np.float64)
+    A /= np.maximum(1.0, np.linalg.norm(A, axis=1, keepdims=True))  # Assumption 1
+    A = A.astype(np.float32)
+    x0 = oracle.sgd(A, pr.y, pr.loss, B1, ETA1, 0.0, K0, SEED)
+    ds = G.Dataset(torch.from_numpy(A).cuda(), torch.from_numpy(pr.y).cuda(), pr.loss, "f32")
+    yield request.param, pr.loss, A, pr.y, x0, ds
+    ds.close()
+
+
+@pytest.mark.parametrize("recipe,acc,st,gop,vop,impl", STEP_MODES)
+def test_recipe_one_outer_step_within_theorem_budget(step_case, recipe, acc, st, gop, vop,
+                                                     impl):
+    name, loss, A, y, x0, ds = step_case
+    xT = _round_t(x0, st)
+    x = torch.from_numpy(xT.copy()).cuda()
+    ds.ca_sgd(x, S1, B1, ETA1, 0.0, S1, SEED, first_iter=K0, gram_dtype=gop, gemv_dtype=vop,
+              gram_impl=impl, accumulate=acc, state_dtype=st)
+    ds.sync()
+    xg = x.cpu().numpy().astype(np.float64)
+    assert np.array_equal(_round_t(xg, st), xg.astype(np.float32))  # the state stays in T
+
+    idx = oracle.sample_indices(SEED, 0, K0 * B1, S1 * B1, M1)
+    Y = A[idx].astype(np.float64)
+    yI = y[idx].astype(np.float64)
+    z, _, _ = le.exact_step(Y, yI, xT.astype(np.float64), loss, ETA1, S1, B1)
+    c32 = (10.0 + 2.35 * float(np.max(np.abs(yI * z)))) if loss == le.LOGISTIC else 2.0
+    uT = U_ST[st]
+    u_acc = 2.0 ** -11 if acc == "f16" else U32
+    u_acc_g = 2.0 ** -11 if impl in (3, 4) else U32
+    if uT:
+        u_c, u_sig, C_delta, u_x = uT + 2 * U32, uT, 1.0 + uT + c32 * U32 / uT, uT + 2 * U32
+    else:
+        u_c, u_sig, C_delta, u_x = U32, U32, c32, U32
+    ev = le.local_error(Y, yI, xT.astype(np.float64), loss, ETA1, S1, B1,
+                        gamma_r=le.gamma_mixed(N1, U_OP[vop], u_acc) + uT,
+                        gamma_G=le.gamma_mixed(N1, U_OP[gop], u_acc_g) + uT,
+                        u_c=u_c, u_sigma=u_sig, C_delta=C_delta,
+                        gamma_g=le.gamma_mixed(S1 * B1, U_OP[vop], u_acc) + uT, u_x=u_x)
+    hyp = ev["omega"] <= 0.5 and ev["tau_G"] <= 0.5
+    dev = float(np.linalg.norm(xg - ev["x_s"]))
+    print(f"{name} recipe {recipe} acc={acc} state={st} gram={gop}/{impl} gemv={vop}: "
+          f"|x_gpu - x_s| = {dev:.3e}, sum E = {ev['sum']:.3e} (ratio {dev / ev['sum']:.2e}), "
+          f"tau_G = {ev['tau_G']:.2e}, omega = {ev['omega']:.2e}")
+    if name == "lsq" and impl in (3, 4):
+        assert not hyp and np.isfinite(dev), (ev["omega"], ev["tau_G"], dev)
+        return
+    assert hyp, (ev["omega"], ev["tau_G"])
+    assert 0.0 < dev <= 2.0 * ev["sum"], (dev, ev["sum"])
+
+
+def test_recipe_partial_outer_step(step_case):
+    """iters not a multiple of s: the last outer step runs iters mod s inner
+    steps; the result is finite, stays in T and is near the FP64 oracle's."""
+    name, loss, A, y, x0, ds = step_case
+    s, it = 8, 8 * 2 + 3
+    xT = _round_t(x0, "bf16")
+    x = torch.from_numpy(xT.copy()).cuda()
+    ds.ca_sgd(x, s, B1, ETA1, 0.0, it, SEED, first_iter=K0, gram_dtype="bf16",
+              state_dtype="bf16")
+    ds.sync()
+    xg = x.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(xg))
+    assert np.array_equal(_round_t(xg, "bf16"), xg.astype(np.float32))
+    xo = oracle.sgd(A, y, loss, B1, ETA1, 0.0, it, SEED, x0=xT.astype(np.float64),
+                    first_iter=K0)
+    moved = float(np.linalg.norm(xo - xT))
+    dev = float(np.linalg.norm(xg - xo))
+    print(f"{name} recipe I, {it} iterations at s={s}: |x_gpu - x_oracle| = {dev:.3e}, "
+          f"|x_oracle - x0| = {moved:.3e}, |x0| = {np.linalg.norm(xT):.3f}")
+    # three roundings of the weights to BF16 (at most 2^-8 |x| each, one per
+    # outer step) and the update's relative error from BF16 operands
+    assert dev <= 4 * 2.0 ** -8 * float(np.linalg.norm(xT)) + 0.05 * moved
+
+
+# ----------------------------------------------------------------------------
+# The end-to-end gap to FP32 CA-SGD
+# ----------------------------------------------------------------------------
+M, N, B, S, H, LAM = 65536, 4096, 32, 16, 200, 1e-4
+CASES = {"logistic": (lambda: synth.logistic_planted(M, N, seed=31, lam=LAM), 0.5),
+         "lsq": (lambda: synth.lsq_planted(M, N, seed=32, noise=0.1, lam=LAM), 0.5),
+         "poisson": (lambda: synth.poisson_planted(M, N, seed=33, lam=LAM), 0.05)}
+E2E_MODES = [pytest.param("f16", "f32", "f16", id="F"), pytest.param("f16", "f16", "f16", id="H"),
+             pytest.param("f32", "bf16", "bf16", id="I")]
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def e2e_case(request, G):
+    make, eta = CASES[request.param]
+    pr = make()
+    ds = G.Dataset(torch.from_numpy(pr.A).cuda(), torch.from_numpy(pr.y).cuda(), pr.loss, "f32")
+    yield request.param, eta, ds
+    ds.close()
+
+
+@pytest.mark.parametrize("acc,st,op", E2E_MODES)
+def test_recipe_end_to_end_gap(e2e_case, acc, st, op):
+    name, eta, ds = e2e_case
+    stall = st == "bf16" and name in ("lsq", "poisson")
+    l0 = ds.loss_value(torch.zeros(N, dtype=torch.float32, device="cuda"), LAM)
+    worst = 0.0
+    for seed in range(3):
+        xa = torch.zeros(N, dtype=torch.float32, device="cuda")
+        xl = torch.zeros(N, dtype=torch.float32, device="cuda")
+        ds.ca_sgd(xa, S, B, eta, LAM, H * S, seed)
+        ds.ca_sgd(xl, S, B, eta, LAM, H * S, seed, gram_dtype=op, accumulate=acc, state_dtype=st)
+        ds.sync()
+        la, ll = ds.loss_value(xa, LAM), ds.loss_value(xl, LAM)
+        gap = abs(ll - la) / abs(la)
+        worst = max(worst, gap)
+        print(f"recipe acc={acc} state={st} {name} seed={seed}: L_FP32={la:.8g} L_low={ll:.8g} "
+              f"gap={gap:.2e}")
+        if stall:
+            assert la < ll < l0, (seed, la, ll, l0)
+    if not stall:
+        assert worst <= 5e-3, (name, acc, st, worst)
