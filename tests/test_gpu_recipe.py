@@ -15,8 +15,15 @@ the same rows, with the slots of these kernels' rounding points (T the state
 type, u_T its unit roundoff, u_in the operand rounding, FP32 storage):
   gamma_r  2 u_in + gamma_n(u_acc), plus u_T for the margin's rounding to T;
   gamma_G  2 u_in + gamma_n(u_acc of the Gram), plus u_T for G read in T;
-  u_c      u_T + 2^-23 (the FP32 combination, then its rounding to T; FP32
-           state: 2^-24);
+  u_c      with FP16 sums in the recurrence (Recipe H proper): u_T + 2^-23
+           (the FP16 accumulation, the FP32 combination, then the rounding
+           of z to T).  With FP32 sums and a narrow state: 2^-23, and the
+           two roundings to T after the sum go to the slots whose quantities
+           they perturb: the correction's rounding (|t| <= (H_L |d|)) adds
+           u_T to gamma_G, and z's rounding adds u_T to gamma_r (its margin
+           part) and u_T to gamma_G (its correction part).  (Charging them to
+           u_c would put gamma_{(s-1)b}(u_T) past its domain for BF16 at
+           (s-1) b = 448.)  FP32 state: 2^-24;
   u_sigma  u_T with C_delta = 1 + u_T + C32 2^-24 / u_T, C32 the FP32
            evaluation's constant of the fused path's budget (logistic
            10 + 2.35 M, least squares 2); FP32 state: 2^-24 with C32;
@@ -153,13 +160,17 @@ def test_recipe_one_outer_step_within_theorem_budget(step_case, recipe, acc, st,
     uT = U_ST[st]
     u_acc = 2.0 ** -11 if acc == "f16" else U32
     u_acc_g = 2.0 ** -11 if impl in (3, 4) else U32
-    if uT:
+    x_r, x_G = uT, uT  # the margin's and G's roundings to T
+    if uT and acc == "f16":
         u_c, u_sig, C_delta, u_x = uT + 2 * U32, uT, 1.0 + uT + c32 * U32 / uT, uT + 2 * U32
+    elif uT:
+        u_c, u_sig, C_delta, u_x = 2 * U32, uT, 1.0 + uT + c32 * U32 / uT, uT + 2 * U32
+        x_r, x_G = 2 * uT, 3 * uT
     else:
         u_c, u_sig, C_delta, u_x = U32, U32, c32, U32
     ev = le.local_error(Y, yI, xT.astype(np.float64), loss, ETA1, S1, B1,
-                        gamma_r=le.gamma_mixed(N1, U_OP[vop], u_acc) + uT,
-                        gamma_G=le.gamma_mixed(N1, U_OP[gop], u_acc_g) + uT,
+                        gamma_r=le.gamma_mixed(N1, U_OP[vop], u_acc) + x_r,
+                        gamma_G=le.gamma_mixed(N1, U_OP[gop], u_acc_g) + x_G,
                         u_c=u_c, u_sigma=u_sig, C_delta=C_delta,
                         gamma_g=le.gamma_mixed(S1 * B1, U_OP[vop], u_acc) + uT, u_x=u_x)
     hyp = ev["omega"] <= 0.5 and ev["tau_G"] <= 0.5
