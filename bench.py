@@ -175,7 +175,8 @@ def _src_hash(*files):
 KERNEL_FILES = {"gather": "paper_2606_18463_gb300/csrc/k_gather.cu",
                 "gram": "paper_2606_18463_gb300/csrc/k_gram_tc.cu",
                 "gram_simt": "paper_2606_18463_gb300/csrc/k_gram_simt.cu",
-                "chain": "paper_2606_18463_gb300/csrc/k_chain.cu"}
+                "chain": "paper_2606_18463_gb300/csrc/k_chain.cu",
+                "chain_stream": "paper_2606_18463_gb300/csrc/k_chain_stream.cu"}
 
 
 def _traffic(kernel: str, workload: str):
@@ -267,7 +268,7 @@ E_BYTES = {"f32": 4, "tf32": 4, "bf16": 2, "f16": 2, "e4m3": 1}
 
 
 def roofline(kms, kl, ms_run, T, s, b, n, e_A, gram, peaks, clocks, gram_impl=2,
-             workload=None):
+             workload=None, chain_impl=1):
     """Roofline of one run: T_roof over the run (gathered bytes at HBM, Gram
     flops at the Gram type's sustained peak, the slower per outer iteration)
     against the measured run time, and the dominant kernel's own fraction
@@ -295,6 +296,8 @@ def roofline(kms, kl, ms_run, T, s, b, n, e_A, gram, peaks, clocks, gram_impl=2,
         peak, unit, bound = peaks["hbm"], "GB/s", "hbm"
         psrc = f"{peaks['src']} HBM copy"
     kern = names[dom] if not (names[dom] == "gram" and simt) else "gram_simt"
+    if kern == "chain" and chain_impl == 2:
+        kern = "chain_stream"
     return {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "peak_source": psrc,
             "traffic": _traffic(kern, workload) if workload else None,
@@ -323,7 +326,7 @@ def time_run(stream, torch, fn, reps=2):
 
 
 def leg(ds, stream, torch, glm, peaks, clocks, *, name, s, b, eta, lam, T, seed, e_A, gram,
-        n, x, reps=2, **opts):
+        n, x, reps=2, workload=None, **opts):
     """One timed configuration on an existing dataset handle."""
     o = dict(opts, gram_dtype=gram, timing=1)
 
@@ -342,7 +345,8 @@ def leg(ds, stream, torch, glm, peaks, clocks, *, name, s, b, eta, lam, T, seed,
          "cluster": plan.cluster, "launches_per_run": plan.launches,
          "final_loss": ds.loss_value(x, lam)}
     r["roofline"] = roofline(kms, kl, ms, T, s, b, n, e_A, gram, peaks, clocks,
-                             gram_impl=plan.gram_impl)
+                             gram_impl=plan.gram_impl, chain_impl=plan.chain_impl,
+                             workload=workload)
     return r
 
 

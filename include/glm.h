@@ -45,6 +45,8 @@ extern "C" {
 #define GLM_ENONFINITE 4    /* a NaN or Inf was produced on the device         */
 #define GLM_ETIMEOUT 5      /* a bounded device wait gave up                   */
 #define GLM_EUNSUPPORTED 6  /* valid request this build does not support       */
+#define GLM_EBOUNDS 7       /* checked builds only: a kernel's computed index
+                               fell outside its buffer; the access was skipped */
 
 /* ---- losses (paper Sec. 2.1) -------------------------------------------- */
 #define GLM_LOGISTIC 0      /* labels must be -1 or +1 */
@@ -66,6 +68,12 @@ const char *glm_last_error(void);
 
 /* Library version string. */
 const char *glm_version(void);
+
+/* 1 when this library was built with -DGLM_CHECKED (every kernel tests its
+ * computed indices against their buffers, records an index outside them as
+ * GLM_EBOUNDS at the next glm_sync or glm_batch_run and skips the access),
+ * else 0.  The checked build is a test instrument: slower, same results. */
+int glm_checked_build(void);
 
 /* ---- dataset handles ----------------------------------------------------- */
 

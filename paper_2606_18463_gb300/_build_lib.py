@@ -18,6 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libglm.so")
+CHECKED_LIB = os.path.join(BUILD, "libglm_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,14 +45,22 @@ def _deps_mtime():
 
 
 def build(verbose: bool = False, force: bool = False, jobs: int | None = None,
-          extra_flags=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+          extra_flags=(), checked: bool = False) -> str:
+    """Compile and link libglm.so; with checked=True the bounds-checked
+    variant libglm_checked.so (-DGLM_CHECKED: kernels test their computed
+    indices and report GLM_EBOUNDS instead of accessing outside a buffer),
+    from objects of its own."""
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib = CHECKED_LIB if checked else LIB
+    if checked:
+        extra_flags = (*extra_flags, "-DGLM_CHECKED")
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     hdr = _deps_mtime()
     srcs = sources()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if (not force and os.path.exists(obj)
                 and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr)):
             return obj, False
@@ -69,15 +78,15 @@ def build(verbose: bool = False, force: bool = False, jobs: int | None = None,
     with cf.ThreadPoolExecutor(max_workers=jobs or min(8, len(srcs))) as ex:
         results = list(ex.map(compile_one, srcs))
     objs = [o for o, _ in results]
-    relink = any(c for _, c in results) or not os.path.exists(LIB) or force
+    relink = any(c for _, c in results) or not os.path.exists(lib) or force
     if relink:
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -380,6 +380,7 @@ int enqueue_run(Handle *h, const RunPlan &p, cudaStream_t st) {
     ga.m = h->m;
     ga.n = h->n;
     ga.rows = rows;
+    ga.flag = h->dflag;
     ga.q0 = (uint64_t)((p.first_iter + it0) * p.b);
     ga.seed = p.seed;
     ga.problem = p.problem;
@@ -517,6 +518,14 @@ extern "C" {
 const char *glm_last_error(void) { return g_last_error.c_str(); }
 
 const char *glm_version(void) { return "libglm 0.1 (sm_103a)"; }
+
+int glm_checked_build(void) {
+#ifdef GLM_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 void glm_create_opts_default(glm_create_opts *o) {
   if (!o) return;
@@ -706,6 +715,8 @@ int glm_sync(glm_handle hh) {
   if (flag) {
     GLM_CUDA_TRY(cudaMemsetAsync(h->dflag, 0, 4, h->stream));
     GLM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (flag & FLAG_BOUNDS)
+      return set_error(GLM_EBOUNDS, "a kernel index fell outside its buffer (checked build)");
     if (flag & FLAG_TIMEOUT) return set_error(GLM_ETIMEOUT, "a bounded device wait gave up");
     return set_error(GLM_ENONFINITE, "a run produced a non-finite margin, residual or iterate");
   }

@@ -400,6 +400,7 @@ int sample_rows(Batch &B, int p, int64_t rows, std::vector<float> &out) {
   memset(&ga, 0, sizeof(ga));
   ga.A = h->A; ga.lda = h->lda; ga.a_dt = h->dtype; ga.colscale = h->colscale;
   ga.y = h->y; ga.m = h->m; ga.n = h->n; ga.rows = rows;
+  ga.flag = h->dflag;
   ga.q0 = 0; ga.seed = B.pr[p].seed; ga.problem = (uint64_t)p;
   ga.out1 = d; ga.dt1 = GLM_F32; ga.ld1 = ld;
   ga.ylab = lab; ga.lab_sb = rows; ga.lab_sbp = round_up(rows, 4);
@@ -729,9 +730,12 @@ int glm_batch_run(glm_batch bt, float *const *xs, int *status) {
   if (gflag) {  // a Gram launch gave up a bounded wait: every problem's G is suspect
     GLM_CUDA_TRY(cudaMemset(B->bflag, 0, sizeof(unsigned)));
     for (int p = 0; p < B->P; ++p) glm_sync(B->pr[p].h);  // clear the problems' flags
+    const int code = (gflag & FLAG_BOUNDS) ? GLM_EBOUNDS : GLM_ETIMEOUT;
     if (status)
-      for (int p = 0; p < B->P; ++p) status[p] = GLM_ETIMEOUT;
-    return set_error(GLM_ETIMEOUT, "a Gram launch of the batch gave up a bounded device wait");
+      for (int p = 0; p < B->P; ++p) status[p] = code;
+    return set_error(code, code == GLM_EBOUNDS
+                               ? "a Gram launch of the batch indexed outside G (checked build)"
+                               : "a Gram launch of the batch gave up a bounded device wait");
   }
   for (int p = 0; p < B->P; ++p) {
     const int rc = glm_sync(B->pr[p].h);  // reads and clears the problem's flag

@@ -44,7 +44,21 @@ enum : unsigned {
   FLAG_NONFINITE = 1u,
   FLAG_BAD_LABEL = 2u,
   FLAG_TIMEOUT = 4u,
+  FLAG_BOUNDS = 8u,  // checked builds: an index fell outside its buffer
 };
+
+// Checked builds (-DGLM_CHECKED): a kernel tests each computed index against
+// its buffer before the access; an index outside it raises FLAG_BOUNDS (when
+// the launch has a flag word) and the access is skipped.  Other builds
+// compile the test away.
+#ifdef GLM_CHECKED
+__device__ __forceinline__ bool in_bounds(bool ok, unsigned *flag) {
+  if (!ok && flag) atomicOr(flag, FLAG_BOUNDS);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool in_bounds(bool, unsigned *) { return true; }
+#endif
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) on the device.
@@ -427,6 +441,7 @@ struct GatherArgs {
   void *out2; int dt2; int64_t ld2;            // optional second output
   float *ylab; float *rscale;                  // labels / row scales (E4M3)
   int64_t lab_sb, lab_sbp;                     // label of row r at (r/sb)*sbp + r%sb
+  unsigned *flag;                              // device flag word (checked builds), or null
 };
 int launch_gather(const GatherArgs &a, cudaStream_t st);
 

@@ -245,6 +245,7 @@ int run_recipe(Handle *h, int s, int64_t b, float eta, float lambda, int64_t ite
     ga.A = h->A; ga.lda = h->lda; ga.a_dt = h->dtype; ga.colscale = h->colscale;
     ga.A8 = h->A8; ga.rs8 = h->rowscale8; ga.lda8 = h->lda8;
     ga.y = h->y; ga.m = h->m; ga.n = h->n; ga.rows = rows;
+    ga.flag = h->dflag;
     ga.q0 = (uint64_t)((first + t) * b); ga.seed = seed; ga.problem = problem;
     ga.out1 = h->ygram[0].ptr; ga.dt1 = gram_dt; ga.ld1 = ld_gram;
     if (ld_gemv) { ga.out2 = h->ygemv[0].ptr; ga.dt2 = gemv_dt; ga.ld2 = ld_gemv; }

@@ -273,6 +273,7 @@ int glm_slab_partial(glm_handle hh, int s, int64_t b, int sh, uint64_t seed, int
   ga.A = h->A; ga.lda = h->lda; ga.a_dt = h->dtype; ga.colscale = h->colscale;
   ga.A8 = h->A8; ga.rs8 = h->rowscale8; ga.lda8 = h->lda8;
   ga.y = h->y; ga.m = h->m; ga.n = h->n; ga.rows = rows;
+  ga.flag = h->dflag;
   ga.q0 = (uint64_t)(first_iter * b); ga.seed = seed; ga.problem = st.problem;
   ga.out1 = h->ygram[0].ptr; ga.dt1 = st.gram_dt; ga.ld1 = st.ld_gram;
   if (st.ld_gemv) {

@@ -46,6 +46,7 @@ k_gather_batch(const BatchItem *__restrict__ items) {
     int32_t idx = 0;
     if (lane == 0) idx = draw_row(it.seed, it.problem, it.q0 + (uint64_t)row, (uint64_t)it.m);
     idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (!in_bounds(idx >= 0 && idx < it.m, lane == 0 ? it.flag : nullptr)) continue;
     const TS *src = A + (int64_t)idx * it.lda;
     for (int64_t c = (int64_t)lane * 8; c < it.ldy; c += 256) {
       float v[8];

@@ -434,8 +434,11 @@ k_chain(const __grid_constant__ ChainArgs a) {
     int64_t soff = 0;  // floats into the slot
     for (int j = 1; j < shh; ++j) {
       const int64_t ldj = gram_ld(j, b);
-      bulk_load(dst + (uint32_t)(soff * 4), Gs + gram_off(j, b) + l0 * ldj,
-                (uint32_t)(nown * ldj * 4), bar);
+      if (in_bounds(Gs + gram_off(j, b) + (l0 + nown) * ldj <= a.G + (int64_t)a.nouter * gsz &&
+                        soff + nown * ldj <= L.gslot_floats,
+                    a.flag))
+        bulk_load(dst + (uint32_t)(soff * 4), Gs + gram_off(j, b) + l0 * ldj,
+                  (uint32_t)(nown * ldj * 4), bar);
       soff += (int64_t)rpb * ldj;
     }
     ++s_fills[kMaxSlots + slot];
@@ -447,8 +450,12 @@ k_chain(const __grid_constant__ ChainArgs a) {
     const int64_t ldj = gram_ld(j, b);
     const uint32_t bar = full_g0 + 8 * slot;
     mbar_arrive_expect_tx(bar, (uint32_t)(nown * ldj * 4));
-    bulk_load(smem_u32(gbuf + slot * L.gslot_floats),
-              a.G + (int64_t)hh * gsz + gram_off(j, b) + l0 * ldj, (uint32_t)(nown * ldj * 4), bar);
+    if (in_bounds(hh < a.nouter &&
+                      gram_off(j, b) + (l0 + nown) * ldj <= gsz && nown * ldj <= L.gslot_floats,
+                  a.flag))
+      bulk_load(smem_u32(gbuf + slot * L.gslot_floats),
+                a.G + (int64_t)hh * gsz + gram_off(j, b) + l0 * ldj, (uint32_t)(nown * ldj * 4),
+                bar);
     ++s_fills[kMaxSlots + slot];
   };
   if (tid == 0 && ns > 0)  // the Y tensor map is read by every Y fill
@@ -687,6 +694,9 @@ k_chain(const __grid_constant__ ChainArgs a) {
               gofs = gslot * L.gslot_floats;
             } else {
               gofs = gram_off(j, b) + l0 * ldj;
+              if (!in_bounds(h < a.nouter && gofs + (int64_t)nown * ldj <= gsz,
+                             lane == 0 ? a.flag : nullptr))
+                gofs = 0;  // (checked builds) read a row range inside this step's G
             }
           }
           const int jb = (int)(j * b);

@@ -491,7 +491,10 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
           const uint32_t full = fullG + 8 * gslot;
           if (lane == 0) mbar_arrive_expect_tx(full, wb * (uint32_t)nown);
           __syncwarp();
-          if (lane < nown)  // one row of the piece per lane
+          if (lane < nown &&  // one row of the piece per lane
+              in_bounds(grow + c0 + (int64_t)lane * gld + wb / 4 <= a.G + (int64_t)a.nouter * gsz &&
+                            c0 + (int64_t)wb / 4 <= gld,
+                        a.flag))
             bulk_load(dst + (uint32_t)(lane * L_PC * 4), grow + c0 + (int64_t)lane * gld, wb, full);
           ++gk;
           if (++gslot == L_NG) { gslot = 0; gphase ^= 1u; }

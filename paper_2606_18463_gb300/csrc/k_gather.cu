@@ -21,6 +21,7 @@ k_gather(GatherArgs a) {
     int32_t idx = 0;
     if (lane == 0) idx = draw_row(a.seed, a.problem, a.q0 + (uint64_t)row, (uint64_t)a.m);
     idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (!in_bounds(idx >= 0 && idx < a.m, lane == 0 ? a.flag : nullptr)) continue;
     const TS *src = A + (int64_t)idx * a.lda;
     char *d1 = static_cast<char *>(a.out1) + row * a.ld1 * elem_bytes(a.dt1);
     char *d2 = a.out2 ? static_cast<char *>(a.out2) + row * a.ld2 * elem_bytes(a.dt2)
@@ -61,6 +62,7 @@ k_gather_e4m3(GatherArgs a) {
     int32_t idx = 0;
     if (lane == 0) idx = draw_row(a.seed, a.problem, a.q0 + (uint64_t)row, (uint64_t)a.m);
     idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (!in_bounds(idx >= 0 && idx < a.m, lane == 0 ? a.flag : nullptr)) continue;
     const uint8_t *s8 = a.A8 + (int64_t)idx * a.lda8;
     uint8_t *d1 = static_cast<uint8_t *>(a.out1) + row * a.ld1;
     for (int64_t c = (int64_t)lane * 16; c < a.ld1; c += 512) {

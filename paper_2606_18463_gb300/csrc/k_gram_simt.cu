@@ -121,7 +121,8 @@ k_gram_simt(GramArgs a) {
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int64_t col = c0 + tx * 4 + jj;
-      if (col < j * a.b) {
+      if (col < j * a.b &&
+          in_bounds(grow + col < a.G + a.nouter * gram_size(a.s, a.b), a.flag)) {
         float v = (float)acc[i][jj];
         if (a.rs) v = v * sr * a.rs[g * sb + col];
         grow[col] = v;

@@ -339,6 +339,10 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
         }
         const int64_t c0 = tl.ti * kN + cc * 32;
         if (!row_ok || c0 >= limit) continue;
+        if (!in_bounds(tl.g < a.nouter && grow + min(c0 + 32, limit) <=
+                           a.G + a.nouter * gram_size(a.s, a.b),
+                       a.flag))
+          continue;
         if (DT == GLM_E4M3) {
 #pragma unroll
           for (int i = 0; i < 32; ++i)

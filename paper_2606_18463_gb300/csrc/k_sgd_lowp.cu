@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(kThreads) k_sgd_lowp(LowpArgs a) {
     if (tid < b) {
       const int32_t r = draw_row(a.seed, a.problem, a.q0 + (uint64_t)(t * b + tid),
                                  (uint64_t)a.m);
-      sidx[tid] = r;
-      sy[tid] = a.y[r];
+      const int32_t rr = in_bounds(r >= 0 && r < a.m, a.flag) ? r : 0;
+      sidx[tid] = rr;
+      sy[tid] = a.y[rr];
     }
     __syncthreads();
     // margins and residuals: warp w takes rows w, w + 32, ...; lane l sums

@@ -17,12 +17,17 @@ import os
 import threading
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libglm.so")
+# GLM_LIBRARY names another build of the same ABI (the bounds-checked
+# _build/libglm_checked.so); default: the package's libglm.so
+LIB_PATH = os.environ.get("GLM_LIBRARY") or os.path.join(_PKG, "_build", "libglm.so")
+CHECKED_LIB_PATH = os.path.join(_PKG, "_build", "libglm_checked.so")
 
 # status codes
-GLM_OK, GLM_EINVAL, GLM_ENOMEM, GLM_ECUDA, GLM_ENONFINITE, GLM_ETIMEOUT, GLM_EUNSUPPORTED = range(7)
+(GLM_OK, GLM_EINVAL, GLM_ENOMEM, GLM_ECUDA, GLM_ENONFINITE, GLM_ETIMEOUT, GLM_EUNSUPPORTED,
+ GLM_EBOUNDS) = range(8)
 STATUS_NAMES = {0: "GLM_OK", 1: "GLM_EINVAL", 2: "GLM_ENOMEM", 3: "GLM_ECUDA",
-                4: "GLM_ENONFINITE", 5: "GLM_ETIMEOUT", 6: "GLM_EUNSUPPORTED"}
+                4: "GLM_ENONFINITE", 5: "GLM_ETIMEOUT", 6: "GLM_EUNSUPPORTED",
+                7: "GLM_EBOUNDS"}
 # losses
 GLM_LOGISTIC, GLM_LSQ, GLM_POISSON = 0, 1, 2
 # element types
@@ -32,7 +37,8 @@ DTYPES = {"f32": GLM_F32, "bf16": GLM_BF16, "f16": GLM_F16, "tf32": GLM_TF32,
 
 # every symbol include/glm.h declares (checked by the CPU test-suite)
 EXPORTED = [
-    "glm_last_error", "glm_version", "glm_create_opts_default", "glm_create",
+    "glm_last_error", "glm_version", "glm_checked_build", "glm_create_opts_default",
+    "glm_create",
     "glm_create_ex", "glm_destroy", "glm_shape", "glm_stream", "glm_sync",
     "glm_ca_opts_default", "glm_sgd_run", "glm_sgd_run_ex", "glm_sgd_lowp_run", "glm_ca_sgd_run",
     "glm_ca_sgd_run_ex", "glm_ca_plan", "glm_kernel_times", "glm_loss",
@@ -108,6 +114,7 @@ def load():
         sig = {
             "glm_last_error": ([], ctypes.c_char_p),
             "glm_version": ([], ctypes.c_char_p),
+            "glm_checked_build": ([], i32),
             "glm_create_opts_default": ([ctypes.POINTER(glm_create_opts)], None),
             "glm_create": ([vp, vp, i64, i64, i32, i32, ctypes.POINTER(vp)], i32),
             "glm_create_ex": ([vp, vp, i64, i64, i32, i32, ctypes.POINTER(glm_create_opts),

@@ -50,3 +50,18 @@ def test_no_cpu_fallback_in_product():
 def test_build_flags_target_sm103a():
     from paper_2606_18463_gb300 import _build_lib
     assert "arch=compute_103a,code=sm_103a" in _build_lib.ARCH
+
+
+def test_checked_variant_exports_and_reports_itself():
+    """The bounds-checked build (-DGLM_CHECKED) exports the same ABI and says
+    so through glm_checked_build(); the product library says it is not."""
+    import ctypes
+    from paper_2606_18463_gb300 import _build_lib, glm
+    if not os.path.exists(glm.CHECKED_LIB_PATH):
+        _build_lib.build(checked=True)
+    chk = ctypes.CDLL(glm.CHECKED_LIB_PATH)
+    for name in _header_functions():
+        assert hasattr(chk, name), name
+    chk.glm_checked_build.restype = ctypes.c_int
+    assert chk.glm_checked_build() == 1
+    assert glm.load().glm_checked_build() == 0
