@@ -452,7 +452,10 @@ typedef struct {
                          tau_G = K_s L_sigma alpha (2 u_A + gamma_G) ||H_L||
                          (paper Sec. 5.2), bounded from one gathered outer
                          step of up to four problems of each n, is at most
-                         tau_bound (the theorem needs <= 1/2).              */
+                         tau_bound (the theorem needs <= 1/2).  A narrower
+                         type serves the Gram only: s = 1 keeps the storage
+                         type, so a narrower type is kept only if every n
+                         has an admitted s > 1.                             */
 } glm_batch_opts;
 
 void glm_batch_opts_default(glm_batch_opts *o);

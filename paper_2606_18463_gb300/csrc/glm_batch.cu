@@ -13,12 +13,15 @@
 // per-problem table lives in device memory, so new iterate pointers only
 // rewrite the table.
 //
-// Autotuner: it chooses what leaves the exact-arithmetic iterate unchanged
-// -- the s-step length (CA-SGD equals SGD for every s) and the Gram kernel --
-// and never the mini-batch b (part of the problem) or the operand precision
-// (which would trade accuracy silently).  For every n among the problems left
-// to it, it times one round of each candidate s in {1, 2, 4, 8, 16} on up to 32 of
-// those problems (scratch iterates) and keeps the fastest in samples/s.
+// Autotuner: by default it chooses what leaves the exact-arithmetic iterate
+// unchanged -- the s-step length (CA-SGD equals SGD for every s) and the Gram
+// kernel and tile -- and never the mini-batch b (part of the problem).  The
+// Gram operand type is chosen only under a caller bound on Theorem 1's
+// hypothesis figure tau_G (glm_batch_opts.tau_bound), estimated from sampled
+// rows, so that no precision is traded without the caller's consent.  For
+// every n among the problems left to it, it times one round of each admitted
+// candidate on up to 32 of those problems (scratch iterates) and keeps the
+// fastest in samples/s (see autotune() below).
 #include <math.h>
 #include <string.h>
 
@@ -426,8 +429,9 @@ int sample_rows(Batch &B, int p, int64_t rows, std::vector<float> &out) {
 // round of each candidate (s, Gram kernel) -- s in {1, 2, 4, 8, 16}; SIMT,
 // tcgen05 128 x 128 or 128 x 256 tiles -- and keeps the fastest in samples
 // per second.  With a bound, (s, type) pairs whose estimated tau_G exceeds it
-// are not timed (s = 1 has no Gram and is always admissible), and the type
-// kept is the one with the shortest estimated run over all problems.
+// are not timed; s = 1 (no Gram) runs only on the storage type's operands, so
+// a narrower type must have an admitted s > 1 for every n; and the type kept
+// is the one with the shortest estimated run over all problems.
 int autotune(Batch &B) {
   std::map<int64_t, std::vector<int>> by_n;  // problems left to the tuner, by n
   for (int p = 0; p < B.P; ++p)
@@ -472,6 +476,10 @@ int autotune(Batch &B) {
     if (rc != GLM_OK) break;
     B.gdt = T;
     const double u_in = operand_roundoff(T, B.dtype), u_A = unit_roundoff(B.dtype);
+    // a type narrower than the storage is chosen for its Gram only: plain SGD
+    // (s = 1, no Gram) keeps the storage type's exact operands, so such a type
+    // needs an admitted s > 1 for every n
+    const bool narrowed = B.tau_bound > 0.0 && B.gdt_free && u_in > 0.0;
     std::map<int64_t, Choice> ch;
     double total = 0.0;
     for (auto &kv : by_n) {
@@ -481,6 +489,7 @@ int autotune(Batch &B) {
       Choice c;
       for (int si = 0; si < 5 && rc == GLM_OK; ++si) {
         const int sv = svals[si];
+        if (narrowed && sv == 1) continue;
         if (B.tau_bound > 0.0 && sv > 1) {  // the prior: every sampled problem admits it
           double tmax = 0.0;
           for (size_t k = 0; k < kv.second.size() && k < 4; ++k) {
@@ -507,7 +516,7 @@ int autotune(Batch &B) {
       ch[kv.first] = c;
       double work = 0.0;  // samples of all this n's problems at the chosen rate
       for (int p : kv.second) work += (double)B.pr[p].iters * (double)B.pr[p].b;
-      total += work / std::max(c.rate, 1e-12);
+      total += c.rate > 0.0 ? work / c.rate : INFINITY;  // no admitted candidate
     }
     if (rc == GLM_OK && total < best_total) {
       best_total = total;
