@@ -100,13 +100,18 @@ __host__ __device__ inline SLayout stream_layout(int64_t n, int64_t b, int s, in
   L.off_rem = take((size_t)4 * 16 * 4, 16);
   const size_t fixed = (off + 1023) / 1024 * 1024;
   // rings, in order of preference: double-buffered margin and update tiles
-  // and three G pieces of 32 KB, then smaller slots before single buffering
+  // and three G pieces of 32 KB; then 32 KB G pieces with single-buffered
+  // margin and update tiles, ahead of smaller pieces, since the recurrence
+  // pays a fixed cost per piece (long blocks: 2,016 pieces of 256 columns per
+  // step at b = 256 ran 28 % slower than half as many of 512); then smaller
+  // slots.  At most kMaxRing slots per ring (the barrier block's size).
   L.slot = 0;
   L.NM = L.NU = L.NG = 0;
-  const int cand[12][4] = {{2, 2, 3, 32}, {2, 2, 2, 32}, {2, 2, 3, 24}, {2, 2, 2, 24},
-                           {2, 2, 4, 16}, {2, 2, 3, 16}, {2, 2, 2, 16}, {1, 2, 2, 32},
-                           {1, 2, 2, 16}, {2, 2, 2, 8}, {1, 1, 2, 16}, {1, 1, 2, 8}};
-  for (int q = 0; q < 12 && !L.slot; ++q) {
+  const int cand[13][4] = {{2, 2, 3, 32}, {2, 2, 2, 32}, {2, 2, 3, 24}, {2, 2, 2, 24},
+                           {1, 1, 2, 32}, {2, 2, 4, 16}, {2, 2, 3, 16}, {2, 2, 2, 16},
+                           {1, 2, 2, 32}, {1, 2, 2, 16}, {2, 2, 2, 8}, {1, 1, 2, 16},
+                           {1, 1, 2, 8}};
+  for (int q = 0; q < 13 && !L.slot; ++q) {
     const size_t sl = (size_t)cand[q][3] * 1024;
     const int nr = cand[q][0] + cand[q][1] + cand[q][2];
     if (fixed + (size_t)nr * sl + 1024 <= kSmemMax) {
@@ -879,7 +884,8 @@ bool chain_stream_ok(const ChainArgs &a) {
   if (a.cluster < 1 || a.cluster > 16) return false;
   const SLayout L = layout_of(a);
   return L.slot > 0 && L.rpb <= 32 && L.nc <= 256 && L.TM >= 1 && L.TU >= 1 &&
-         (a.s < 2 || L.PC >= 4) && L.total <= kSmemMax && a.s <= 256;
+         (a.s < 2 || L.PC >= 4) && L.total <= kSmemMax && a.s <= 256 &&
+         L.NM <= kMaxRing && L.NU <= kMaxRing && L.NG <= kMaxRing;
 }
 
 int launch_chain_stream(const ChainArgs &a, cudaStream_t st) {
