@@ -325,6 +325,41 @@ def time_run(stream, torch, fn, reps=2):
     return statistics.median(ts)
 
 
+def gram_isolated(torch, glm, peaks):
+    """The tcgen05 Gram alone (glm_gram_lower, BF16 operands, FP32
+    accumulation) at the paper's roofline shape -- n = 16,384, b = 32, s in
+    {2, 8, 16, 32, 64}, one outer step -- and at one outer step of the wide and
+    the large least-squares shapes: strictly block-lower flops b^2 s (s-1) n
+    over the CUDA-event time of one launch (median of 5 after a warm-up),
+    against the measured BF16 burst peak.  Random N(0,1) rows, L2-resident
+    operands (one outer step's rows fit in L2), as a kernel timed alone."""
+    from paper_2606_18463_gb300 import accounting as acc
+    out = []
+    shapes = [("paper roofline shape", 1, s, 32, 16384) for s in (2, 8, 16, 32, 64)]
+    shapes += [("wide, 8 outer steps", 8, 16, 128, 2048), ("large lsq, 1 outer step", 1, 64, 256, 1024)]
+    for name, nouter, s, b, n in shapes:
+        torch.manual_seed(0)
+        Y = torch.randn(nouter * s * b, n, device="cuda").to(torch.bfloat16)
+        G = torch.empty(nouter * acc.gram_lower_floats(s, b), device="cuda")
+        run = lambda: glm.glm_gram_lower(Y, glm.GLM_BF16, nouter, s, b, n, n, None, G, 2)  # noqa
+        run()
+        ts = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = sorted(ts)[2]
+        tf = acc.gram_flops(s, b, n) * nouter / (ms / 1e3) / 1e12
+        out.append({"shape": name, "s": s, "b": b, "n": n, "nouter": nouter, "ms": ms,
+                    "tflops": tf, "frac_of_bf16_burst": tf / peaks["bf16"]})
+        del Y, G
+    return out
+
+
 def leg(ds, stream, torch, glm, peaks, clocks, *, name, s, b, eta, lam, T, seed, e_A, gram,
         n, x, reps=2, workload=None, **opts):
     """One timed configuration on an existing dataset handle."""
@@ -571,6 +606,8 @@ def main():
             out["wide"] = wide_legs(args, torch, synth, glm, peaks, clocks)
         if not args.no_large:
             out["large"] = large_legs(args, torch, synth, glm, peaks, clocks)
+    if not args.no_extras and ws == 1:
+        out["gram_isolated"] = gram_isolated(torch, glm, peaks)
     if not args.no_extras and not args.no_batch:
         out["batched"] = _batched(args, torch, synth, glm, rank, peaks)
     if rank == 0:

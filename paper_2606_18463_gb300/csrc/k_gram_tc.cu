@@ -51,6 +51,7 @@ struct TcArgs {
   long long probe;        // > 0: failure-path probe wait before the first MMA
   int64_t nouter, rows, b, n, ld;
   int s, dt, nk;          // nk: K chunks
+  int ksplit, kper;       // K split into ksplit ranges of kper chunks (1: none)
 };
 
 // ---- PTX wrappers (tcgen05 / TMEM) -------------------------------------------
@@ -229,7 +230,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
 
   const int64_t sb = (int64_t)a.s * a.b;
   const int64_t P = tiles_per_outer<kN>(sb);
-  const int64_t ntiles = a.nouter * P;
+  const int64_t ntiles = a.nouter * P * a.ksplit;  // work units: (tile, K range)
   volatile int *vabort = &s_abort;
 
   if (warp == 0) {
@@ -238,10 +239,11 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
       int64_t it = 0;
       for (int64_t t = blockIdx.x; t < ntiles && !*vabort; t += gridDim.x) {
         Tile tl;
-        if (!tile_at<kN>(a, P, t, tl)) continue;
+        if (!tile_at<kN>(a, P, t / a.ksplit, tl)) continue;
+        const int kb = (int)(t % a.ksplit) * a.kper, ke = min(a.nk, kb + a.kper);
         const int32_t ya = (int32_t)(tl.g * sb + tl.tj * kTile);
         const int32_t yb = (int32_t)(tl.g * sb + tl.ti * kN);
-        for (int kc = 0; kc < a.nk; ++kc, ++it) {
+        for (int kc = kb; kc < ke; ++kc, ++it) {
           const int st = (int)(it % kStages);
           if (it >= kStages &&
               !wait_or_abort(empty0 + 8 * st, (uint32_t)((it / kStages - 1) & 1), vabort)) {
@@ -273,7 +275,8 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
       if (a.probe > 0 && !mbar_wait_bounded(probe_bar, 0, a.probe)) atomicOr(&s_abort, 1);
       for (int64_t t = blockIdx.x; t < ntiles && !*vabort; t += gridDim.x) {
         Tile tl;
-        if (!tile_at<kN>(a, P, t, tl)) continue;
+        if (!tile_at<kN>(a, P, t / a.ksplit, tl)) continue;
+        const int kb = (int)(t % a.ksplit) * a.kper, ke = min(a.nk, kb + a.kper);
         const int buf = (int)(tc & 1);
         if (tc >= 2 &&
             !wait_or_abort(tempty0 + 8 * buf, (uint32_t)((tc / 2 - 1) & 1), vabort)) {
@@ -283,7 +286,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
         tc_fence_after();
         const uint32_t tmem_d = tmem_base + (uint32_t)(buf * kN);
         bool ok = true;
-        for (int kc = 0; kc < a.nk; ++kc, ++it) {
+        for (int kc = kb; kc < ke; ++kc, ++it) {
           const int st = (int)(it % kStages);
           if (!wait_or_abort(full0 + 8 * st, (uint32_t)((it / kStages) & 1), vabort)) {
             atomicOr(&s_abort, 1);
@@ -295,7 +298,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
           const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + kOperandBytes);
 #pragma unroll
           for (int k = 0; k < kChunkBytes / 32; ++k)  // 32 bytes of K per MMA
-            tc_mma<DT>(tmem_d, da + 2 * k, db + 2 * k, idesc, (kc | k) != 0);
+            tc_mma<DT>(tmem_d, da + 2 * k, db + 2 * k, idesc, (kc != kb) || k != 0);
           tc_commit(empty0 + 8 * st);  // stage free once these MMAs have read it
         }
         if (!ok) break;
@@ -314,7 +317,7 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
     int64_t tc = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       Tile tl;
-      if (!tile_at<kN>(a, P, t, tl)) continue;
+      if (!tile_at<kN>(a, P, t / a.ksplit, tl)) continue;
       const int buf = (int)(tc & 1);
       if (!wait_or_abort(tfull0 + 8 * buf, (uint32_t)((tc / 2) & 1), vabort)) {
         atomicOr(&s_abort, 1);
@@ -348,7 +351,20 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
           for (int i = 0; i < 32; ++i)
             v[i] *= srow * ((c0 + i < limit) ? __ldg(a.rs + tl.g * sb + c0 + i) : 0.f);
         }
-        if (c0 + 32 <= limit) {
+        if (a.ksplit > 1) {  // partial sums over one K range: added into zeroed G
+          // (16-byte vector atomics: rows start on 16-byte boundaries, c0 % 32 == 0)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (c0 + 4 * q + 4 <= limit) {
+              atomicAdd(reinterpret_cast<float4 *>(grow + c0 + 4 * q),
+                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                if (c0 + 4 * q + i < limit) atomicAdd(grow + c0 + 4 * q + i, v[4 * q + i]);
+            }
+          }
+        } else if (c0 + 32 <= limit) {
           float4 *d = reinterpret_cast<float4 *>(grow + c0);
 #pragma unroll
           for (int q = 0; q < 8; ++q)
@@ -431,6 +447,24 @@ int launch_gram_tc_impl(const GramArgs &g, cudaStream_t st, bool acc16) {
   // wide tiles unless they would leave SMs idle (few, long-K tiles), or as
   // the caller asks (the batched autotuner times both)
   const int64_t wide = g.nouter * tiles_per_outer<256>(sb);
+  a.ksplit = 1;
+  a.kper = a.nk;
+  // Few wide tiles over a long K (the paper's roofline shape: n = 16,384 over
+  // a few thousand rows) leave most SMs idle: split K instead, ranges of at
+  // least 16 chunks, each range's partial sums added into a zeroed G.  The
+  // order of those additions varies from run to run; every entry keeps its
+  // Higham bound.  Not for the FP16-accumulate Gram, whose single FP16 sum is
+  // what Recipe F prescribes, nor when the caller fixes the tile.
+  if (!acc16 && g.tile_n == 0 && wide < sms && a.nk >= 32) {
+    int64_t ks = sms / (wide > 0 ? wide : 1);
+    if (ks > a.nk / 16) ks = a.nk / 16;
+    if (ks > 1) {
+      a.kper = (int)((a.nk + ks - 1) / ks);
+      a.ksplit = (a.nk + a.kper - 1) / a.kper;
+      GLM_CUDA_TRY(cudaMemsetAsync(g.G, 0, (size_t)g.nouter * gram_size(g.s, g.b) * 4, st));
+      return launch_n<256>(a, sms, wide * a.ksplit, st, acc16);
+    }
+  }
   if (g.tile_n == 256 || (g.tile_n == 0 && wide >= sms))
     return launch_n<256>(a, sms, wide, st, acc16);
   return launch_n<128>(a, sms, g.nouter * tiles_per_outer<128>(sb), st, acc16);

@@ -231,7 +231,8 @@ def _gram_size(s, b):
 
 @pytest.mark.parametrize("dt", ["f32", "tf32", "bf16", "f16", "e4m3"])
 @pytest.mark.parametrize("impl", [1, 0])
-@pytest.mark.parametrize("nouter,s,b,n", [(3, 4, 16, 100), (2, 16, 64, 512), (1, 3, 130, 70)])
+@pytest.mark.parametrize("nouter,s,b,n", [(3, 4, 16, 100), (2, 16, 64, 512), (1, 3, 130, 70),
+                                          (1, 8, 32, 4096)])  # few tiles, long K: split K
 def test_gram_lower_bound(G, dt, impl, nouter, s, b, n):
     rng = np.random.default_rng(s * 1000 + b + n)
     sb = s * b
