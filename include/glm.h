@@ -361,8 +361,12 @@ int glm_storage_read(glm_handle h, int64_t row0, int64_t rows, void *A_out,
  * floats of a row hold no result.  impl: 0 auto, 1 SIMT FP32, 2 tcgen05, 3
  * SIMT with FP16 accumulation, 4 tcgen05 with an FP16 accumulator (3 and 4:
  * GLM_F16 only, else GLM_EINVAL).  ld must be a multiple of 64 for impl 2
- * and 4.  stream: cudaStream_t or NULL (legacy default
- * stream).
+ * and 4.  With impl 2 (or 0 choosing it) a shape with fewer 128 x 256 tiles
+ * than SMs and at least 4,096 bytes of K per row splits K across SMs: the
+ * whole G range is zeroed on the stream first (padding included) and the
+ * partial sums are added atomically, so the last bits of an entry can differ
+ * between runs; each entry stays within the FP32-accumulation bound.
+ * stream: cudaStream_t or NULL (legacy default stream).
  */
 int glm_gram_lower(const void *Y, int dtype, int64_t nouter, int s, int64_t b,
                    int64_t n, int64_t ld, const float *row_scale, float *G,
