@@ -95,6 +95,14 @@ template <int DT> __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64
   }
 }
 
+// 32-byte global store of eight floats (the address must be 32-byte aligned).
+__device__ __forceinline__ void st_global_v8(float *p, float a, float b, float c, float d,
+                                             float e, float f, float g, float h) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d), "f"(e), "f"(f), "f"(g), "f"(h)
+               : "memory");
+}
+
 // 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
@@ -364,6 +372,14 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
                 if (c0 + 4 * q + i < limit) atomicAdd(grow + c0 + 4 * q + i, v[4 * q + i]);
             }
           }
+        } else if (c0 + 32 <= limit && (reinterpret_cast<uintptr_t>(grow + c0) & 31) == 0) {
+          // 32-byte stores: each lane writes its own row, so a store instruction
+          // touches 32 rows; wider stores halve the instructions the SM's
+          // store path has to split (the epilogue bounds the K = 1,024 tiles)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            st_global_v8(grow + c0 + 8 * q, v[8 * q], v[8 * q + 1], v[8 * q + 2], v[8 * q + 3],
+                         v[8 * q + 4], v[8 * q + 5], v[8 * q + 6], v[8 * q + 7]);
         } else if (c0 + 32 <= limit) {
           float4 *d = reinterpret_cast<float4 *>(grow + c0);
 #pragma unroll
