@@ -103,9 +103,10 @@ __device__ __forceinline__ void st_global_v8(float *p, float a, float b, float c
                : "memory");
 }
 
-// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Asynchronous form: starts the load of 32 columns into r; r is valid only
+// after tmem_ld_wait(r) (which takes r as an operand, so that no use of r
+// can be scheduled before the wait).
+__device__ __forceinline__ void tmem_ld32_start(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -117,9 +118,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
         "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])
+               :: "memory");
 }
 
 // Bounded wait that also gives up once another role of the CTA has aborted
@@ -338,22 +346,22 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
       const int64_t limit = j * a.b;                           // columns < j b
       float *grow = a.G + tl.g * gram_size(a.s, a.b) + gram_off(j, a.b) + l * gram_ld(j, a.b);
       const float srow = (DT == GLM_E4M3 && row_ok) ? a.rs[tl.g * sb + rho] : 1.f;
-#pragma unroll 1
-      for (int cc = 0; cc < kN / 32; ++cc) {
+      // chunk cc's 32 columns of this lane's row: scale and store
+      auto store_chunk = [&](uint32_t (&r)[32], int cc) {
         float v[32];
-        tmem_ld32(tmem_base + (uint32_t)(buf * kN + cc * 32) + ((uint32_t)(quad * 32) << 16),
-                  v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
         if (kAcc16) {  // F16 accumulator: the low 16 bits of each column
 #pragma unroll
           for (int i = 0; i < 32; ++i)
             v[i] = __half2float(__ushort_as_half((unsigned short)(__float_as_uint(v[i]) & 0xFFFFu)));
         }
         const int64_t c0 = tl.ti * kN + cc * 32;
-        if (!row_ok || c0 >= limit) continue;
+        if (!row_ok || c0 >= limit) return;
         if (!in_bounds(tl.g < a.nouter && grow + min(c0 + 32, limit) <=
                            a.G + a.nouter * gram_size(a.s, a.b),
                        a.flag))
-          continue;
+          return;
         if (DT == GLM_E4M3) {
 #pragma unroll
           for (int i = 0; i < 32; ++i)
@@ -390,6 +398,24 @@ k_gram_tc(const __grid_constant__ TcArgs a) {
           for (int i = 0; i < 32; ++i)
             if (c0 + i < limit) grow[c0 + i] = v[i];
         }
+      };
+      // the next chunk's TMEM load is in flight while this chunk is stored
+      auto taddr = [&](int cc) {
+        return tmem_base + (uint32_t)(buf * kN + cc * 32) + ((uint32_t)(quad * 32) << 16);
+      };
+      uint32_t ra[32], rb[32];
+      tmem_ld32_start(taddr(0), ra);
+      tmem_ld_wait(ra);
+#pragma unroll 1
+      for (int cc = 0; cc < kN / 32; cc += 2) {  // kN / 32 is even
+        tmem_ld32_start(taddr(cc + 1), rb);
+        store_chunk(ra, cc);
+        __syncwarp();  // the TMEM loads and waits are warp-wide (.sync.aligned)
+        tmem_ld_wait(rb);
+        if (cc + 2 < kN / 32) tmem_ld32_start(taddr(cc + 2), ra);
+        store_chunk(rb, cc + 1);
+        __syncwarp();
+        if (cc + 2 < kN / 32) tmem_ld_wait(ra);
       }
       tc_fence_before();
       __syncwarp();
