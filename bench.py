@@ -25,8 +25,8 @@ and the 256-problem batched workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU: one process per GPU (torchrun); each rank runs an independent
-replica (the single-fit path is not sharded on this build), value = all
-ranks' samples / max-over-ranks time.
+replica of the single fit (the column partition of glm_slab_* is not used
+here), value = all ranks' samples / max-over-ranks time.
 """
 from __future__ import annotations
 

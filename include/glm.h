@@ -44,7 +44,7 @@ extern "C" {
 #define GLM_ECUDA 3         /* a CUDA runtime / driver call failed             */
 #define GLM_ENONFINITE 4    /* a NaN or Inf was produced on the device         */
 #define GLM_ETIMEOUT 5      /* a bounded device wait gave up                   */
-#define GLM_EUNSUPPORTED 6  /* valid request this build does not support       */
+#define GLM_EUNSUPPORTED 6  /* valid request the library does not support      */
 #define GLM_EBOUNDS 7       /* checked builds only: a kernel's computed index
                                fell outside its buffer; the access was skipped */
 
