@@ -311,6 +311,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int3
       ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(bar) : "memory");
 }
 
+// TMA: 4D tiled load of box {x, y, z, w} coordinates (x innermost) into
+// shared memory, completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int32_t x, int32_t y,
+                                            int32_t z, int32_t w, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar) : "memory");
+}
+
+// TMA: prefetch a 4D box into L2 (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_4d(const void *tmap, int32_t x, int32_t y, int32_t z,
+                                                int32_t w) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];"
+               ::"l"(tmap), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
 // Bulk (non-tensor) copy global -> shared; size and both addresses must be
 // multiples of 16 bytes.
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
@@ -329,6 +346,12 @@ int make_tmap_2d(CUtensorMap *out, const void *base, int dt, uint64_t inner, uin
 int make_tmap_2d_sw128(CUtensorMap *out, const void *base, int dt, uint64_t inner,
                        uint64_t outer, uint64_t row_bytes, uint32_t box_inner,
                        uint32_t box_outer);
+
+// Host: encode a 4D FP32 tensor map (dims[0] innermost; byte strides of
+// dims 1..3, multiples of 16) with a box of box[0..3] elements, no swizzle,
+// zero fill out of bounds.
+int make_tmap_4d_f32(CUtensorMap *out, const void *base, const uint64_t dims[4],
+                     const uint64_t strides[3], const uint32_t box[4]);
 
 // Bulk prefetch of [src, src + bytes) from global memory into L2 (src
 // 16-byte aligned, bytes a multiple of 16); no data reach shared memory.

@@ -59,6 +59,8 @@ constexpr int kWork = 11;        // update warps 4..14
 constexpr long long kWaitBudget = 4000000000ll;
 constexpr size_t kSmemMax = 227 * 1024 - 1024;
 constexpr int kMaxRing = 4;
+constexpr int kMaxGmap = 63;     // G tensor maps (block rows 1..s-1, s <= 64)
+constexpr int kPrefetch = 8;     // G pieces prefetched into L2 ahead of their copies
 
 struct SLayout {
   int C, rpb, nc, npad, mbw, mshift, mbox, TM, TU, PC, NM, NU, NG, V, ngrp;
@@ -314,6 +316,13 @@ struct StreamArgs {
   float alpha;
   long long probe;
   double cpow[257], cinv[257];
+  // gtma != 0: G pieces arrive as one TMA box each through gmap[j - 1], a 4D
+  // view of block row j -- {ginner columns, ld_j / ginner column groups, b
+  // rows, outer steps} -- whose box {ginner, PC / ginner, rpb, 1} lands as
+  // the piece's rpb rows of PC floats, the layout the row copies produce
+  int gtma, ginner;
+  int gpf;  // 1: also prefetch G pieces into L2 (gtma; a step's G far larger than L2)
+  CUtensorMap gmap[kMaxGmap];
 };
 
 template <typename TY, int MODE>
@@ -470,6 +479,31 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
       };
       gstart();
       if (nown == 0) { mh = a.nouter; gh = a.nouter; }
+      // a step's G far larger than L2 (it streams from HBM): a second G
+      // cursor runs kPrefetch pieces ahead of the copies into shared memory
+      // and prefetches those boxes into L2, so that each piece's copy meets
+      // L2 rather than HBM latency
+      int ph = 0, pj = 1, pp = 0, pf = 0;  // cursor and pieces prefetched
+      auto pnext = [&]() {                 // advance (ph, pj, pp) by one piece
+        if ((int64_t)(pp + 1) * L_PC < (int64_t)pj * b) {
+          ++pp;
+        } else {
+          pp = 0;
+          ++pj;
+        }
+        while (ph < a.nouter && pj >= shof(ph)) { ++ph; pj = 1; }
+      };
+      while (ph < a.nouter && pj >= shof(ph)) { ++ph; pj = 1; }
+      if (nown == 0) ph = a.nouter;
+      auto prefetch_to = [&](int target) {  // until pf == target (lane 0)
+        for (; pf < target && ph < a.nouter; ++pf) {
+          if (in_bounds(pj >= 1 && pj - 1 < kMaxGmap, a.flag))
+            tma_prefetch_4d(&a.gmap[pj - 1], 0, (int32_t)((int64_t)pp * L_PC / a.ginner),
+                            (int32_t)l0, (int32_t)ph);
+          pnext();
+        }
+      };
+      if (a.gpf && lane == 0) prefetch_to(kPrefetch);
       const uint32_t mbytes = (uint32_t)((size_t)L_mbox * L_mbw * L_TM * sizeof(TY));
       const uint32_t mboxb = (uint32_t)((size_t)L_mbw * L_TM * sizeof(TY));
       const uint32_t ubytes = (uint32_t)((size_t)nc * L_TU * sizeof(TY));
@@ -494,13 +528,23 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
           const uint32_t wb = (uint32_t)(round_up(w, 4) * 4);
           const uint32_t dst = smem_u32(ringG + (size_t)gslot * L_slot);
           const uint32_t full = fullG + 8 * gslot;
-          if (lane == 0) mbar_arrive_expect_tx(full, wb * (uint32_t)nown);
-          __syncwarp();
-          if (lane < nown &&  // one row of the piece per lane
-              in_bounds(grow + c0 + (int64_t)lane * gld + wb / 4 <= a.G + (int64_t)a.nouter * gsz &&
-                            c0 + (int64_t)wb / 4 <= gld,
-                        a.flag))
-            bulk_load(dst + (uint32_t)(lane * L_PC * 4), grow + c0 + (int64_t)lane * gld, wb, full);
+          if (a.gtma) {  // the whole piece in one box (rows past b read as zeros)
+            if (lane == 0) {
+              mbar_arrive_expect_tx(full, (uint32_t)(L_PC * L.rpb * 4));
+              if (in_bounds(gj >= 1 && gj - 1 < kMaxGmap, a.flag))
+                tma_load_4d(dst, &a.gmap[gj - 1], 0, (int32_t)(c0 / a.ginner), (int32_t)l0,
+                            (int32_t)gh, full);
+              if (a.gpf) prefetch_to(gk + 1 + kPrefetch);
+            }
+          } else {
+            if (lane == 0) mbar_arrive_expect_tx(full, wb * (uint32_t)nown);
+            __syncwarp();
+            if (lane < nown &&  // one row of the piece per lane
+                in_bounds(grow + c0 + (int64_t)lane * gld + wb / 4 <= a.G + (int64_t)a.nouter * gsz &&
+                              c0 + (int64_t)wb / 4 <= gld,
+                          a.flag))
+              bulk_load(dst + (uint32_t)(lane * L_PC * 4), grow + c0 + (int64_t)lane * gld, wb, full);
+          }
           ++gk;
           if (++gslot == L_NG) { gslot = 0; gphase ^= 1u; }
           did = true;
@@ -919,6 +963,27 @@ int launch_chain_stream(const ChainArgs &a, cudaStream_t st) {
   for (int j = 0; j <= a.s; ++j) {
     sa.cpow[j] = a.cpow[j];
     sa.cinv[j] = a.cinv[j];
+  }
+  // G pieces by TMA: every block row's width (j b) and the piece width PC
+  // are multiples of the box's inner width (at most 256 columns)
+  int gi = 256;
+  while (gi >= 8 && (a.b % gi != 0 || L.PC % gi != 0)) gi /= 2;
+  if (a.s >= 2 && a.s - 1 <= kMaxGmap && gi >= 8 && L.PC / gi <= 256 && L.rpb <= 256) {
+    const int64_t gsz = gram_size(a.s, a.b);
+    for (int j = 1; j < a.s; ++j) {
+      const int64_t ldj = gram_ld(j, a.b);
+      const uint64_t dims[4] = {(uint64_t)gi, (uint64_t)(ldj / gi), (uint64_t)a.b,
+                                (uint64_t)a.nouter};
+      const uint64_t strides[3] = {(uint64_t)gi * 4, (uint64_t)ldj * 4, (uint64_t)gsz * 4};
+      const uint32_t box[4] = {(uint32_t)gi, (uint32_t)(L.PC / gi), (uint32_t)L.rpb, 1u};
+      GLM_TRY(make_tmap_4d_f32(&sa.gmap[j - 1], a.G + gram_off(j, a.b), dims, strides, box));
+    }
+    sa.gtma = 1;
+    sa.ginner = gi;
+    // measured: prefetching pays where a step's G streams from HBM (the
+    // large least-squares shape, 528 MB) and costs a little where it stays
+    // in L2 (the wide shape at s = 32, 32 MB)
+    sa.gpf = gsz * 4 > (64ll << 20);
   }
   switch (a.dt) {
   case GLM_F32: case GLM_TF32: return launch_sy<float>(sa, L, a.cluster, a.rec64, st);
