@@ -11,8 +11,11 @@
 //           (TMA boxes of 256 columns);
 //   ring U  update tiles: every row of each block, this CTA's column slice
 //           (TMA boxes of nc columns);
-//   ring G  pieces of this CTA's own rows of each block row of G_L (bulk
-//           copies, PC columns at a time, in column order).
+//   ring G  pieces of this CTA's own rows of each block row of G_L, PC
+//           columns at a time, in column order: one 4D TMA box per piece
+//           where b and PC are multiples of its inner width, else one bulk
+//           copy per row; when a step's G is far larger than L2, the boxes
+//           are also prefetched into L2 a few pieces ahead.
 // Work split in the cluster:
 //   * rows: CTA k owns rows [k rpb, (k+1) rpb) of every b-row block; it
 //     computes their full margins r = Y x (x is replicated in every CTA), and
