@@ -234,8 +234,8 @@ __device__ __forceinline__ float dloss_fast(int loss, float z, float y) {
 // Partial correction dots of up to four own rows (piece rows q0 + i, row
 // stride PC floats in shared memory) with the history uh[c0 ..) over `w`
 // columns; lane-strided 4-column chunks and a scalar tail.  MODE 0: FP32,
-// 1: FP64, 2: FP32 products with Kahan-compensated per-lane sums (two per
-// row, combined in FP64 with the lanes').
+// 1: FP64, 2: FP32 products with Kahan-compensated per-lane sums (MODE 0 and
+// 2 keep two sums per row, over alternate columns; FP64 one).
 template <int MODE>
 struct DotAcc {
   using TA = typename std::conditional<MODE == 1, double, float>::type;
@@ -297,10 +297,14 @@ __device__ __forceinline__ void piece_dot4(const float *__restrict__ g, int PC, 
           acc.add(i, gv[i].z * u[2]);
           acc.add2(i, gv[i].w * u[3]);
         } else {
+          // FP32: columns x, z and y, w into two sums per row (half-length
+          // FMA chains; measured 2 % faster per outer step on the wide shape)
           acc.s[i] = fma((TA)gv[i].x, u[0], acc.s[i]);
-          acc.s[i] = fma((TA)gv[i].y, u[1], acc.s[i]);
+          if (MODE == 0) acc.c[i] = fma((TA)gv[i].y, u[1], acc.c[i]);
+          else acc.s[i] = fma((TA)gv[i].y, u[1], acc.s[i]);
           acc.s[i] = fma((TA)gv[i].z, u[2], acc.s[i]);
-          acc.s[i] = fma((TA)gv[i].w, u[3], acc.s[i]);
+          if (MODE == 0) acc.c[i] = fma((TA)gv[i].w, u[3], acc.c[i]);
+          else acc.s[i] = fma((TA)gv[i].w, u[3], acc.s[i]);
         }
       }
     }
@@ -749,7 +753,8 @@ k_chain_stream(const __grid_constant__ StreamArgs a) {
               } else {
                 TH v[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = (TH)acc[gi].s[i];
+                for (int i = 0; i < 4; ++i)
+                  v[i] = MODE == 0 ? (TH)(acc[gi].s[i] + acc[gi].c[i]) : (TH)acc[gi].s[i];
                 corr = sum4_t<TH>(v, lane);
               }
               const TH rv = rown[j * rpb + rq];
